@@ -1,0 +1,42 @@
+/*
+ * Oracle RNG: Philox4x32-10, written from its published definition
+ * (J. K. Salmon et al., "Parallel random numbers: as easy as 1, 2, 3", SC'11).
+ * TEST INFRASTRUCTURE ONLY (see oracle.h).
+ *
+ * GPUMCD §II.C.1 uses a combined multiply-with-carry generator; this build
+ * replaces it on both sides by a counter-based generator so that a particle's
+ * random numbers depend only on (seed, history, lineage, draw index).
+ *
+ * One Philox round maps (c0, c1, c2, c3) with key (k0, k1) to
+ *   (hi(M1*c2) ^ c1 ^ k0,  lo(M1*c2),  hi(M0*c0) ^ c3 ^ k1,  lo(M0*c0))
+ * and the key advances by the Weyl increments between rounds.
+ */
+#include "oracle.h"
+
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void om_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0;
+        c1 = n1;
+        c2 = n2;
+        c3 = n3;
+        k0 += PHILOX_W0;
+        k1 += PHILOX_W1;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}

@@ -1,0 +1,219 @@
+"""Pins for the oracle's electron physics (GPUMCD §II.B): restricted stopping
+power, Moller and bremsstrahlung hard events, multiple scattering, the CSDA
+range and energy conservation."""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle
+import workloads as W
+from tests._stats import chi2_pvalue, within_sigma
+
+RE = 2.8179403262e-13
+MC2 = 0.51099895
+ALPHA = 1 / 137.035999084
+NA = 6.02214076e23
+P = W.DEFAULT_PHYSICS
+
+
+def n_e(m):
+    return sum(NA * w / A * Z for Z, A, w in zip(m.Z, m.A, m.w))
+
+
+def test_bethe_collision_stopping_power_textbook():
+    # water, I = 75 eV, no density effect: the Bethe value at 100 keV is 4.115 MeV cm^2/g
+    assert oracle.xs("s_col", W.WATER, 0.1) == pytest.approx(4.115, rel=2e-3)
+    assert oracle.xs("s_col", W.WATER, 0.01) == pytest.approx(22.56, rel=3e-3)
+
+
+@pytest.mark.parametrize("mat", [W.WATER, W.BONE])
+@pytest.mark.parametrize("T", [0.45, 1.0, 4.0, 15.0])
+def test_restricted_loss_equals_moller_energy_integral(mat, T):
+    """S_col(T) - L_col(T, T_c) = n_e int_{T_c/T}^{1/2} eps T dsigma_M/deps deps:
+    the restriction removes exactly the energy carried by knock-ons above T_c."""
+    L = oracle.lib()
+    tc = 0.2
+    lhs = oracle.xs("s_col", mat, T) - oracle.xs("l_col", mat, T, tc)
+    val, _ = integrate.quad(lambda e: e * T * L.om_moller_dsigma_deps(T, e), tc / T, 0.5,
+                            epsabs=0, epsrel=1e-13, limit=200)
+    assert lhs == pytest.approx(n_e(mat) * val, rel=1e-9)
+
+
+def test_restricted_equals_unrestricted_below_twice_cut():
+    for T in (0.25, 0.39):
+        assert oracle.xs("l_col", W.WATER, T, 0.2) == oracle.xs("s_col", W.WATER, T)
+        assert oracle.xs("sigma_moller", W.WATER, T, 0.2) == 0.0
+
+
+@pytest.mark.parametrize("T", [0.5, 2.0, 15.0])
+def test_moller_total_equals_quadrature(T):
+    L = oracle.lib()
+    tc = 0.2
+    val, _ = integrate.quad(lambda e: L.om_moller_dsigma_deps(T, e), tc / T, 0.5, epsabs=0,
+                            epsrel=1e-13, limit=200)
+    assert oracle.xs("sigma_moller", W.WATER, T, tc) == pytest.approx(n_e(W.WATER) * val, rel=1e-10)
+
+
+@pytest.mark.parametrize("T", [0.5, 3.0, 15.0])
+def test_moller_sampler_chi2(T):
+    L = oracle.lib()
+    tc = 0.2
+    eps = oracle.sample("moller", 200_000, 31, T, tc)
+    assert eps.min() >= tc / T and eps.max() <= 0.5
+    grid = np.geomspace(tc / T, 0.5, 20001)
+    assert chi2_pvalue(eps, lambda e: L.om_moller_dsigma_deps(T, e), grid) > 0.01
+
+
+@pytest.mark.parametrize("mat", [W.WATER, W.BONE])
+@pytest.mark.parametrize("T", [0.3, 2.0, 15.0])
+def test_brem_hard_plus_soft_equals_total_radiative(mat, T):
+    kc = 0.01
+    L = oracle.lib()
+    m = oracle.material(mat)
+    f = lambda k: L.om_brem_dsigma_dk(m, T, k)  # noqa: E731
+    hard_energy, _ = integrate.quad(lambda k: k * f(k), kc, T, epsabs=0, epsrel=1e-12, limit=200)
+    soft = oracle.xs("l_rad", mat, T, kc)
+    assert soft + hard_energy == pytest.approx(oracle.xs("s_rad", mat, T), rel=1e-10)
+    hard_n, _ = integrate.quad(f, kc, T, epsabs=0, epsrel=1e-12, limit=200,
+                               points=np.geomspace(kc, T, 12)[1:-1])
+    assert oracle.xs("sigma_brem", mat, T, kc) == pytest.approx(hard_n, rel=1e-9)
+
+
+def test_brem_log_growth_small_cut():
+    """For k_c << T the hard cross-section grows like (4/3)(S_A + S_1/12) ln(T/k_c)."""
+    T = 10.0
+    a = oracle.xs("sigma_brem", W.WATER, T, 1e-4)
+    b = oracle.xs("sigma_brem", W.WATER, T, 1e-5)
+    m = W.WATER
+    SA = sum(NA * w / A * Z * (Z + 1) * math.log(183 * Z ** (-1 / 3)) for Z, A, w in zip(m.Z, m.A, m.w))
+    S1 = sum(NA * w / A * Z * (Z + 1) for Z, A, w in zip(m.Z, m.A, m.w))
+    slope = 4 * ALPHA * RE ** 2 * (4 / 3 * SA + S1 / 9)
+    assert (b - a) / math.log(10.0) == pytest.approx(slope, rel=1e-4)
+
+
+@pytest.mark.parametrize("T", [0.5, 6.0, 15.0])
+def test_brem_sampler_chi2(T):
+    L = oracle.lib()
+    kc = 0.01
+    k = oracle.sample("brem", 200_000, 32, W.BONE, T, kc)
+    assert k.min() >= kc and k.max() <= T
+    m = oracle.material(W.BONE)
+    grid = np.geomspace(kc, T, 20001)
+    assert chi2_pvalue(k, lambda x: L.om_brem_dsigma_dk(m, T, x), grid) > 0.01
+
+
+@pytest.mark.parametrize("mat", [W.WATER, W.BONE])
+@pytest.mark.parametrize("T", [0.2, 1.0, 15.0])
+def test_ms_transport_cross_section_quadrature(mat, T):
+    """(1/lambda_1)/rho = sum_j N_j 2 pi int (1 - cos) dsigma/dOmega dcos for the
+    screened Rutherford cross-section with the Moliere screening parameter."""
+    L = oracle.lib()
+    pc2 = T * (T + 2 * MC2)
+    g = T / MC2 + 1
+    beta2 = 1 - 1 / g ** 2
+    tot = 0.0
+    for Z, A, w in zip(mat.Z, mat.A, mat.w):
+        eta = L.om_ms_screening(Z, T)
+        K = Z * (Z + 1) * RE ** 2 * MC2 ** 2 / (beta2 * pc2)
+        v, _ = integrate.quad(lambda c: (1 - c) * K / (1 - c + 2 * eta) ** 2, -1, 1, epsabs=0,
+                              epsrel=1e-12, limit=400, points=[1 - 20 * eta, 1 - 2000 * eta])
+        tot += NA * w / A * 2 * math.pi * v
+    assert oracle.xs("ms_lambda1_inv", mat, T) == pytest.approx(tot, rel=1e-8)
+
+
+def test_ms_screening_moliere_form():
+    # eta = alpha^2 Z^(2/3) / (4 0.885^2) (mc^2/pc)^2 (1.13 + 3.76 (alpha Z / beta)^2)
+    L = oracle.lib()
+    T, Z = 2.0, 8
+    pc2 = T * (T + 2 * MC2)
+    beta2 = 1 - 1 / (T / MC2 + 1) ** 2
+    eta = ALPHA ** 2 * Z ** (2 / 3) / (4 * 0.885 ** 2) * MC2 ** 2 / pc2 * (
+        1.13 + 3.76 * (ALPHA * Z) ** 2 / beta2)
+    assert L.om_ms_screening(Z, T) == pytest.approx(eta, rel=1e-14)
+
+
+def test_ms_mean_mu_series_matches_direct_form():
+    L = oracle.lib()
+    for a in (990.0, 1000.0, 1010.0):
+        direct = a * ((1 + a) * math.log1p(1 / a) - 1)
+        assert L.om_ms_mean_mu(a) == pytest.approx(direct, rel=1e-9)
+
+
+@pytest.mark.parametrize("g1", [1e-6, 1e-3, 0.05, 0.7, 4.0])
+def test_ms_sampler_mean_deflection(g1):
+    """<1 - cos theta> after G1 transport mean free paths is 1 - exp(-G1)
+    (Goudsmit-Saunderson first moment), and mu follows (mu + a)^-2."""
+    L = oracle.lib()
+    n = 400_000
+    mu = oracle.sample("ms", n, 33, g1)
+    m1 = 2 * mu.mean()
+    s = 2 * mu.std() / math.sqrt(n)
+    assert within_sigma(m1, -math.expm1(-g1), s)
+    a = L.om_ms_solve_a(g1)
+    grid = np.concatenate([[0.0], np.geomspace(1e-14, 1.0, 20000)])
+    assert chi2_pvalue(mu, lambda x: 1.0 / (x + a) ** 2, grid) > 0.01
+
+
+def test_ms_isotropic_limit():
+    from scipy import stats
+    mu = oracle.sample("ms", 200_000, 34, 50.0)
+    assert stats.kstest(mu, "uniform").pvalue > 0.01
+
+
+def _csda_range(mat, T0, T1):
+    val, _ = integrate.quad(lambda t: 1.0 / (oracle.xs("s_col", mat, t) + oracle.xs("s_rad", mat, t)),
+                            T1, T0, epsrel=1e-10, limit=200)
+    return val
+
+
+@pytest.mark.parametrize("E0", [2.0, 10.0])
+def test_csda_track_length(E0):
+    """With hard events off (t_c, k_c above T) and no deflection, the mean path
+    of an electron equals the CSDA integral of dE/S(E) down to where it stops
+    (the condensed-history energy-loss step of §II.B.3)."""
+    n = 3000
+    ph = W.homogeneous((8, 8, 60), 0.5, W.MAT_WATER, 1.0)
+    src = W.pencil(W.ELECTRON, E0, 2.0, 2.0)
+    phys = W.Physics(t_c=100.0, k_c=100.0)
+    res = oracle.simulate(W.MATERIALS, phys, ph, src, n, 3, flags=oracle.FLAG_NO_MS)
+    st = res.stats
+    assert st["n_hard_real"] == 0 and st["n_electrons"] == n
+    t_end = st["e_cut_electron"] / n
+    track = st["track_length_cm"] / n
+    assert track == pytest.approx(_csda_range(W.WATER, E0, t_end), rel=0.01)
+
+
+@pytest.mark.parametrize("cfg", ["c1", "c2e", "c2g", "c3", "slab_e"])
+def test_energy_conservation_tiny_runs(cfg):
+    """Deposited + escaped + rest mass = incident to 1e-9 (FP64 ledger)."""
+    if cfg == "c1":
+        pl = W.config1(n_histories=300)
+    elif cfg == "c2e":
+        pl = W.config2(W.ELECTRON, n_histories=30, n=32, voxel_cm=1.0)
+    elif cfg == "c2g":
+        pl = W.config2(W.PHOTON, n_histories=100, n=32, voxel_cm=1.0)
+    elif cfg == "c3":
+        pl = W.config3(n_histories=200, n=64, voxel_cm=0.8)
+    else:
+        ph = W.z_slabs((16, 16, 40), 0.5, [(2.0, W.MAT_WATER, 1.0), (2.0, W.MAT_LUNG, 0.26),
+                                            (2.0, W.MAT_BONE, 1.85), (1e9, W.MAT_WATER, 1.0)])
+        pl = W.Plan("slab_e", ph, W.pencil(W.ELECTRON, 15.0, 4.0, 4.0), 50, 9)
+    res = oracle.simulate(W.MATERIALS, P, pl.phantom, pl.source, pl.n_histories, pl.seed)
+    st = res.stats
+    tot = st["e_deposited"] + st["e_escaped"] + st["e_rest"]
+    assert tot == pytest.approx(st["e_incident"], rel=1e-9)
+    assert res.sum_e.sum() == pytest.approx(st["e_deposited"], rel=1e-12)
+    assert st["n_histories"] == pl.n_histories
+
+
+def test_history_split_is_exact():
+    """Histories are independent and keyed by index: two halves add up to the
+    whole run (the basis of the multi-process fan-out)."""
+    pl = W.config1(n_histories=400)
+    a = oracle.simulate(W.MATERIALS, P, pl.phantom, pl.source, 400, 1)
+    b1 = oracle.simulate(W.MATERIALS, P, pl.phantom, pl.source, 150, 1)
+    b2 = oracle.simulate(W.MATERIALS, P, pl.phantom, pl.source, 250, 1, hist_begin=150)
+    assert np.allclose(a.sum_e, b1.sum_e + b2.sum_e, rtol=1e-12, atol=1e-12)
+    assert np.allclose(a.sum_e2, b1.sum_e2 + b2.sum_e2, rtol=1e-12, atol=1e-12)

@@ -1,0 +1,61 @@
+"""Checks of the seeded input recipes (workloads/)."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+
+def test_materials_fractions():
+    for m in W.MATERIALS:
+        assert sum(m.w) == pytest.approx(1.0, abs=1e-12)
+        assert len(m.Z) <= W.MAX_ELEMENTS
+    assert W.WATER.w[0] == pytest.approx(0.1119, abs=2e-4)
+
+
+def test_config3_slabs():
+    pl = W.config3(n=256, voxel_cm=0.2)
+    ph = pl.phantom
+    col = ph.mat[:, 0, 0]
+    rho = ph.rho[:, 0, 0]
+    # 3 cm water, 2 cm bone, 6 cm lung, rest water at 0.2 cm voxels
+    assert (col[:15] == W.MAT_WATER).all() and (rho[:15] == 1.0).all()
+    assert (col[15:25] == W.MAT_BONE).all() and np.allclose(rho[15:25], 1.85)
+    assert (col[25:55] == W.MAT_LUNG).all() and np.allclose(rho[25:55], 0.26)
+    assert (col[55:] == W.MAT_WATER).all()
+    e, w = pl.source.spectrum_edges, pl.source.spectrum_weights
+    assert e[0] == pytest.approx(0.1) and e[-1] == pytest.approx(6.0)
+    assert len(w) == 256 and w.sum() == pytest.approx(1.0) and (w >= 0).all()
+
+
+def test_spectrum_is_seeded():
+    a = W.synthetic_6mv_spectrum(seed=3)[1]
+    b = W.synthetic_6mv_spectrum(seed=3)[1]
+    c = W.synthetic_6mv_spectrum(seed=4)[1]
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+
+
+def test_plan_distribution_ranges():
+    specs = W.config4()
+    assert len(specs) == 64
+    for s in specs:
+        assert 64 <= s.n <= 256
+        assert 0.2 <= s.voxel_cm <= 0.5
+        assert 6.0 <= s.energy <= 18.0
+        assert 2.0 <= s.field_cm <= 15.0
+        assert 1e5 <= s.n_histories <= 1e7
+    assert {s.particle for s in specs} == {W.PHOTON, W.ELECTRON}
+
+
+def test_smoothed_noise_phantom():
+    spec = W.config4()[0]
+    ph = W.smoothed_noise(48, 0.4, np.random.default_rng(spec.phantom_seed))
+    assert ph.rho.min() == pytest.approx(0.2, abs=1e-6)
+    assert ph.rho.max() == pytest.approx(2.0, abs=1e-6)
+    assert (ph.mat[ph.rho < 0.6] == W.MAT_LUNG).all()
+    assert (ph.mat[ph.rho > 1.4] == W.MAT_BONE).all()
+
+
+def test_config5_arrivals():
+    reqs = W.config5(count=50, rate_per_s=20.0)
+    t = np.array([r.arrival_s for r in reqs])
+    assert (np.diff(t) > 0).all()
