@@ -1,0 +1,292 @@
+#!/usr/bin/env python
+"""Benchmark: histories/s of the coupled photon-electron transport on the
+paper's timing workload (GPUMCD §II.D / Table "resabsexec"): separate 15 MeV
+10x10 cm^2 parallel beams of 1e6 electrons and 4e6 photons on a 128^3 water
+phantom at 0.25 cm.  One step = both beams, each run from a zeroed tally to
+its FP64 dose and uncertainty on the device.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs its own
+histories (weak scaling, no data-path collective); the time is the max over
+ranks.  ``--impl reference`` times the FP64 CPU oracle on the host cores
+instead (bounded samples of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "histories/s (1e6 e- + 4e6 photons, 15 MeV, 128^3 water, to FP64 dose + sigma)"
+UNIT = "histories/s"
+N_E, N_G = 1_000_000, 4_000_000
+
+# Warp-instructions of useful work per unit, from ncu (smsp__thread_inst_executed.sum / 32
+# divided by the kernel's own event counts) on the same workload: per electron
+# condensed-history step and per photon Woodcock event.  See profiles/.
+INST_PER_E_STEP = None
+INST_PER_PH_EVENT = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(
+        os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def oracle_sample(seconds: float = 12.0, seed0: int = 100):
+    """Times the FP64 oracle (as it stands) on bounded samples of the workload
+    over all host cores: electrons and photons in the 1:4 ratio of the step.
+    Returns (histories/s, cores, description)."""
+    import oracle
+    import workloads as W
+
+    cores = host_cores()
+    pe, pg = W.config2(W.ELECTRON), W.config2(W.PHOTON)
+    n_e, n_g = 150 * cores, 600 * cores
+    done = 0
+    t0 = time.perf_counter()
+    rounds = 0
+    while True:
+        oracle.simulate(W.MATERIALS, W.DEFAULT_PHYSICS, pe.phantom, pe.source, n_e, seed0 + rounds,
+                        processes=cores)
+        oracle.simulate(W.MATERIALS, W.DEFAULT_PHYSICS, pg.phantom, pg.source, n_g, seed0 + rounds,
+                        processes=cores)
+        done += n_e + n_g
+        rounds += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    desc = (f"{rounds} round(s) of {n_e} e- + {n_g} photons (15 MeV, 10x10 cm^2, 128^3 water), "
+            f"{cores} processes")
+    return done / dt, cores, desc
+
+
+def emit(obj):
+    print(json.dumps(obj), flush=True)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(seconds=3.0)
+    vals, descs, cores = [], None, host_cores()
+    t_all = 0.0
+    for i in range(args.steps):
+        v, cores, descs = oracle_sample(seconds=8.0, seed0=1000 + 10 * i)
+        vals.append(v)
+        t_all += (N_E + N_G) / v
+    value = (N_E + N_G) * args.steps / t_all
+    emit({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+          "data": "synthetic",
+          "config": {"workload": "c2_water128_15MeV_e1e6_photon4e6", "parallelism": "host cores"},
+          "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                           "sample": descs},
+          "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1101_1245_gb300 as g
+    import workloads as W
+
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample()  # spawned processes, before the GPU work starts
+
+    pe, pg = W.config2(W.ELECTRON), W.config2(W.PHOTON)
+    nvox = pe.phantom.nvox
+    ctx = g.engine(local)
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+    pid = ctx.create_phantom(pe.phantom)
+    plan_e = ctx.plan_open(pid, pe.source, 1, 32)
+    plan_g = ctx.plan_open(pid, pg.source, 2, 32)
+    out = {k: torch.empty(nvox, dtype=torch.float64, device=dev) for k in ("de", "se", "dg", "sg")}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 2x the 129 MB L2
+
+    def step(i):
+        se = 1_000_003 * (rank + 1) + 2 * i
+        ctx.plan_reset(plan_e, se, sh)
+        ctx.run([plan_e], [N_E], sh)
+        st_e = ctx.plan_result(plan_e, 0.5, out["de"].data_ptr(), out["se"].data_ptr(), sh)
+        ctx.plan_reset(plan_g, se + 1, sh)
+        ctx.run([plan_g], [N_G], sh)
+        st_g = ctx.plan_result(plan_g, 0.5, out["dg"].data_ptr(), out["sg"].data_ptr(), sh)
+        return st_e, st_g
+
+    for i in range(args.warmup):
+        step(-1 - i)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stats = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()  # L2 flush between timed steps (outside the events)
+                ev[i][0].record(stream)
+                stats.append(step(i))
+                ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = (N_E + N_G) * args.steps * world / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers: phantom upload, both
+    # beams, dose and sigma read back into host memory
+    import numpy as np
+    hd = {k: np.empty(nvox) for k in ("de", "se", "dg", "sg")}
+    e2e_t = []
+    for i in range(max(2, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p2 = ctx.create_phantom(pe.phantom)
+        ra = ctx.simulate(p2, pe.source, N_E, 77 + i, nvox=nvox)
+        rb = ctx.simulate(p2, pg.source, N_G, 78 + i, nvox=nvox)
+        ctx.destroy_phantom(p2)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_val = (N_E + N_G) * world / statistics.median(e2e_t)
+    h2d = pe.phantom.mat.nbytes + pe.phantom.rho.nbytes
+    d2h = 4 * nvox * 8
+
+    st_e, st_g = stats[-1]
+    launches = st_e["n_launches"] + st_g["n_launches"] + 2 * 3  # transport + fold, s_thr, ledger sum
+    clocks = clk.summary()
+    steps_e = st_e["n_electron_steps"] + st_g["n_electron_steps"]
+    events_g = st_e["n_photon_events"] + st_g["n_photon_events"]
+    kern_ms = st_e["transport_ms"] + st_g["transport_ms"]
+    import paper_1101_1245_gb300.roofline as rl
+    roof = rl.alu_roofline(steps_e, events_g, kern_ms, clocks.get("sm_mhz"),
+                           torch.cuda.get_device_properties(dev).multi_processor_count)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "c2_water128_15MeV_e1e6_photon4e6",
+                       "phantom": "128^3 water, 0.25 cm", "beams": "15 MeV 10x10 cm^2 e- 1e6, photons 4e6",
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "s05_electron": st_e["s_thr"], "s05_photon": st_g["s_thr"],
+                       "transport_ms_electron": st_e["transport_ms"],
+                       "transport_ms_photon": st_g["transport_ms"],
+                       "ledger_exact": all(s["e_deposited"] + s["e_escaped"] + s["e_rest"] == s["e_incident"]
+                                           for s in (st_e, st_g))},
+            "roofline": roof,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clocks}
+    if cpu:
+        line["cpu_baseline"] = {"value": cpu[0], "unit": UNIT, "cores": cpu[1], "kind": "oracle",
+                                "sample": cpu[2]}
+    if rank == 0:
+        emit(line)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,247 @@
+/*
+ * gpumcd.h - C ABI of the GB300 coupled photon-electron Monte Carlo dose engine.
+ *
+ * The engine follows GPUMCD (Hissoiny, Bouchard, Ozell, Despres): a voxelized
+ * phantom of material ids and densities (§II.C.2), material cross-section and
+ * stopping-power data (§II.C.2), a source of one particle type with a
+ * monoenergetic energy or a spectrum and a beam geometry (§II.C.2, §II.D), a
+ * number of histories (§II.D); the result is the dose per voxel and its
+ * statistical uncertainty (§II.D, the Delta D estimator).
+ *
+ * Conventions, for every call:
+ *  - every call returns a gpumcd_status; no call aborts, traps or exits;
+ *  - input arrays are copied; the caller keeps ownership of everything it passes;
+ *  - output arrays are caller-allocated;
+ *  - pointers documented as "host" are ordinary CPU memory, pointers documented
+ *    as "device" are CUDA device memory of the context's device (for example
+ *    from torch), and `stream` is a cudaStream_t passed as void* (NULL means
+ *    the context's own stream);
+ *  - voxel arrays are ordered x fastest, then y, then z; the beam enters
+ *    through the z = 0 face travelling along +z;
+ *  - dose is in Gy per history (MeV/g x 1.602176634e-10);
+ *  - energies in the ledgers are integers in units of 2^-26 MeV.
+ * A context is not thread-safe: serialize calls on one context.
+ */
+#ifndef GPUMCD_H
+#define GPUMCD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gpumcd_ctx gpumcd_ctx;
+typedef int32_t gpumcd_status;
+
+#define GPUMCD_OK 0
+#define GPUMCD_ERR_INVALID_ARG (-1)    /* a pointer, size or value is out of range */
+#define GPUMCD_ERR_OOM (-2)            /* device allocation failed */
+#define GPUMCD_ERR_CUDA (-3)           /* a CUDA call failed (or no device) */
+#define GPUMCD_ERR_QUEUE_OVERFLOW (-4) /* particle queues full: the run stopped, nothing was dropped silently */
+#define GPUMCD_ERR_TIMEOUT (-5)        /* a bounded device wait gave up */
+#define GPUMCD_ERR_NOT_FOUND (-6)      /* unknown phantom or plan id */
+#define GPUMCD_ERR_BUDGET (-7)         /* the allocation would exceed the context's HBM budget */
+#define GPUMCD_ERR_STATE (-8)          /* a call came in the wrong order (e.g. no materials loaded) */
+
+#define GPUMCD_MAX_MATERIALS 4
+#define GPUMCD_MAX_ELEMENTS 16
+#define GPUMCD_MAX_PLANS_PER_RUN 64
+#define GPUMCD_MAX_SPECTRUM_BINS 1024
+
+#define GPUMCD_PHOTON 0
+#define GPUMCD_ELECTRON 1
+#define GPUMCD_BEAM_PENCIL 0
+#define GPUMCD_BEAM_SQUARE 1
+
+/* Energy unit of the ledgers and of the dose tally: 2^-26 MeV. */
+#define GPUMCD_ENERGY_QUANTUM_MEV (1.0 / 67108864.0)
+
+/* One material: element mass fractions and mean excitation energy
+ * (§II.C.2 composition data).  Z, A (g/mol) and w (mass fraction) for
+ * n_elements <= GPUMCD_MAX_ELEMENTS entries; the w need not be normalized. */
+typedef struct {
+    int32_t n_elements;
+    int32_t Z[GPUMCD_MAX_ELEMENTS];
+    double A[GPUMCD_MAX_ELEMENTS];
+    double w[GPUMCD_MAX_ELEMENTS];
+    double I_eV;
+} gpumcd_material;
+
+/* Transport cut-offs and thresholds in MeV (§II.A P_cut, §II.B E_c/K_cut) and
+ * the step controls: estepe = largest fractional CSDA loss per step (the
+ * e_s-max bound of §II.B.3); e_max = top of the table energy range (<= 20);
+ * nudge_cm = distance added to the voxel-boundary distance of a step. */
+typedef struct {
+    double p_cut, e_abs, t_c, k_c, estepe, e_max, nudge_cm;
+} gpumcd_physics;
+
+/* Source (§II.C.2 initParticle): particle type, beam shape and energy.
+ * A spectrum has n_spectrum bins with n_spectrum+1 increasing edges (host,
+ * MeV) and n_spectrum non-negative weights (host); n_spectrum = 0 selects the
+ * monoenergetic energy_mev.  Pencil beams enter at (center_cm[0],
+ * center_cm[1], 0); square beams are uniform over a field_cm x field_cm square
+ * centred there. */
+typedef struct {
+    int32_t particle;
+    int32_t beam;
+    double energy_mev;
+    int32_t n_spectrum;
+    const double *spectrum_edges;
+    const double *spectrum_weights;
+    double center_cm[2];
+    double field_cm;
+} gpumcd_source;
+
+/* Launch tuning; 0 in a field keeps the current value.  See gpumcd_set_launch. */
+typedef struct {
+    uint32_t block_threads;   /* threads per CTA (multiple of 32, <= 1024) */
+    uint32_t blocks_per_sm;   /* resident CTAs per SM of the persistent grid */
+    uint32_t stack_capacity;  /* per-warp particle stack entries per type */
+    uint32_t switch_high;     /* a warp switches type when the other stack holds this many (= stack_capacity: never) */
+    uint32_t refill_low;      /* ...or when it fills fewer lanes than this and the other type has work */
+    uint32_t chunk;           /* primaries or queued particles a warp claims at once */
+    uint32_t overflow_capacity; /* global overflow queue entries per type */
+    uint32_t flags;           /* GPUMCD_LAUNCH_* */
+} gpumcd_launch;
+
+#define GPUMCD_LAUNCH_WARP_AGGREGATE 1u /* combine a warp's deposits to one voxel into one atomic */
+
+/* Counters of one run.  The ledger satisfies, exactly,
+ * e_deposited + e_escaped + e_rest == e_incident. */
+typedef struct {
+    uint64_t histories;
+    uint64_t e_incident, e_deposited, e_escaped, e_rest;
+    uint64_t n_photon_events, n_photon_real, n_compton, n_photo, n_pair;
+    uint64_t n_electron_steps, n_hard_real, n_hard_fict, n_moller, n_brem;
+    uint64_t n_photons, n_electrons, n_overflow;
+    uint64_t n_spilled;        /* particles moved from warp stacks to the global overflow queue */
+    uint64_t n_sampler_capped; /* rejection samplers stopped at their proposal cap (expected 0) */
+    uint32_t n_launches, n_batches;
+    double transport_ms; /* device time of the transport launches */
+    double d_max_gy;     /* largest voxel dose */
+    double s_thr;        /* mean sigma/D over voxels with D > threshold * D_max */
+} gpumcd_run_stats;
+
+/* Name of a status code; never NULL. */
+const char *gpumcd_status_string(gpumcd_status status);
+
+/* Creates a context on CUDA device `device`.  Device memory the context
+ * allocates (phantoms, tallies, scratch) is limited to hbm_budget_bytes
+ * (0 = no limit).  *out receives the context, or NULL on error. */
+gpumcd_status gpumcd_init(gpumcd_ctx **out, int32_t device, uint64_t hbm_budget_bytes);
+
+/* Frees every resource of the context; NULL is accepted. */
+gpumcd_status gpumcd_destroy(gpumcd_ctx *ctx);
+
+/* Loads n <= GPUMCD_MAX_MATERIALS materials (host array, copied) and the
+ * transport parameters, and builds the cross-section, stopping-power and
+ * multiple-scattering tables on the device in FP64 (stored FP32 on a log
+ * energy grid, §II.C.2).  Phantoms and plans must be destroyed first if any
+ * exist (GPUMCD_ERR_STATE). */
+gpumcd_status gpumcd_load_materials(gpumcd_ctx *ctx, const gpumcd_material *materials, int32_t n,
+                                    const gpumcd_physics *physics);
+
+/* Copies a phantom (§II.C.2: composition ids and densities) to the device.
+ * dims (host, 3 ints >= 1), voxel_cm (host, 3 doubles > 0), material_ids
+ * (host, nx*ny*nz bytes, each < number of loaded materials) and densities
+ * (host, nx*ny*nz floats in (0, 16) g/cm^3).  Densities are kept with a
+ * resolution of 2^-24 g/cm^3.  *phantom_id receives a handle. */
+gpumcd_status gpumcd_create_phantom(gpumcd_ctx *ctx, const int32_t dims[3], const double voxel_cm[3],
+                                    const uint8_t *material_ids, const float *densities,
+                                    int32_t *phantom_id);
+
+/* As gpumcd_create_phantom with device arrays, enqueued on `stream`. */
+gpumcd_status gpumcd_create_phantom_device(gpumcd_ctx *ctx, const int32_t dims[3],
+                                           const double voxel_cm[3], const uint8_t *material_ids,
+                                           const float *densities, void *stream,
+                                           int32_t *phantom_id);
+
+gpumcd_status gpumcd_destroy_phantom(gpumcd_ctx *ctx, int32_t phantom_id);
+
+/* One dose calculation on a resident phantom: n_histories primaries of the
+ * source with random streams keyed by seed.  With target_rel_unc > 0 the run
+ * continues in rounds of n_histories until s_thr (threshold 0.5 D_max) falls
+ * to target_rel_unc or max(16 n_histories, 1e9) histories are done.
+ * dose_out and sigma_out are host arrays of nx*ny*nz doubles (either may be
+ * NULL); stats may be NULL. */
+gpumcd_status gpumcd_simulate(gpumcd_ctx *ctx, int32_t phantom_id, const gpumcd_source *source,
+                              uint64_t n_histories, uint64_t seed, double target_rel_unc,
+                              double *dose_out, double *sigma_out, gpumcd_run_stats *stats);
+
+/* As gpumcd_simulate with device outputs, enqueued on `stream` (the call
+ * still waits for the run to finish before it returns). */
+gpumcd_status gpumcd_simulate_device(gpumcd_ctx *ctx, int32_t phantom_id,
+                                     const gpumcd_source *source, uint64_t n_histories,
+                                     uint64_t seed, double target_rel_unc, double *dose_out,
+                                     double *sigma_out, void *stream, gpumcd_run_stats *stats);
+
+/* ---- plans: the batched and served forms ------------------------------- */
+
+/* Opens a plan: a phantom, a source, a seed and a dose tally of n_batches
+ * (power of two in [8, 64]; 0 = 32) batch copies kept on the device.  The
+ * plan's histories are numbered from 0 and its tally accumulates over runs, so
+ * the result after N histories does not depend on how the runs were split or
+ * on what other plans shared them. */
+gpumcd_status gpumcd_plan_open(gpumcd_ctx *ctx, int32_t phantom_id, const gpumcd_source *source,
+                               uint64_t seed, uint32_t n_batches, int32_t *plan_id);
+
+gpumcd_status gpumcd_plan_close(gpumcd_ctx *ctx, int32_t plan_id);
+
+/* Restarts a plan in place: zeroes its tally and ledger (on `stream`),
+ * numbers its histories from 0 again and keys them with `seed`.  Nothing is
+ * allocated or freed. */
+gpumcd_status gpumcd_plan_reset(gpumcd_ctx *ctx, int32_t plan_id, uint64_t seed, void *stream);
+
+/* One batched persistent launch (sequence): plan plan_ids[i] simulates its next
+ * n_histories[i] histories, for n_plans <= GPUMCD_MAX_PLANS_PER_RUN distinct
+ * plans (host arrays).  Enqueued on `stream`; returns once the launch sequence
+ * has finished. */
+gpumcd_status gpumcd_run(gpumcd_ctx *ctx, int32_t n_plans, const int32_t *plan_ids,
+                         const uint64_t *n_histories, void *stream);
+
+/* FP64 fold of a plan's tally (§II.D): dose and sigma in Gy per history into
+ * device arrays of nx*ny*nz doubles (either may be NULL), plus stats with
+ * s_thr over voxels with dose > threshold_frac * D_max. */
+gpumcd_status gpumcd_plan_result(gpumcd_ctx *ctx, int32_t plan_id, double threshold_frac,
+                                 double *dose_out, double *sigma_out, void *stream,
+                                 gpumcd_run_stats *stats);
+
+/* Histories simulated so far by a plan. */
+gpumcd_status gpumcd_plan_histories(gpumcd_ctx *ctx, int32_t plan_id, uint64_t *histories);
+
+/* Device bytes the context currently holds, and its budget. */
+gpumcd_status gpumcd_memory(gpumcd_ctx *ctx, uint64_t *used_bytes, uint64_t *budget_bytes);
+
+/* ---- launch tuning ------------------------------------------------------ */
+gpumcd_status gpumcd_set_launch(gpumcd_ctx *ctx, const gpumcd_launch *launch);
+gpumcd_status gpumcd_get_launch(gpumcd_ctx *ctx, gpumcd_launch *launch);
+
+/* ---- diagnostics used by the tests ------------------------------------- */
+
+/* Copies the device FP32 tables to host memory.  which = 0: photon tables
+ * [material][mu_total, mu_compton, mu_photo][grid] in cm^2/g; 1: electron
+ * tables [material][L_restricted, Sigma_hard, Sigma_brem, lambda1_inv][grid];
+ * 2: the multiple-scattering ln(a) table; 3: the energy grids
+ * [photon grid | electron grid] in MeV.  With out == NULL only *count is set. */
+gpumcd_status gpumcd_get_tables(gpumcd_ctx *ctx, int32_t which, float *out, int32_t *count);
+
+/* Runs one of the device samplers n times (host output of n floats):
+ * kind 0 Klein-Nishina cos(theta) at photon energy p0; 1 Sauter cos(theta) at
+ * kinetic energy p0; 2 Moller eps at T = p0; 3 bremsstrahlung k at T = p0 in
+ * material `material`; 4 multiple-scattering mu at G1 = p0; 5 source energy
+ * of the spectrum in `source`; 6 Klein-Nishina k'/k at p0. */
+gpumcd_status gpumcd_debug_sample(gpumcd_ctx *ctx, int32_t kind, double p0, int32_t material,
+                                  const gpumcd_source *source, uint64_t n, uint64_t seed,
+                                  float *out);
+
+/* Philox4x32-10 on the device: for i < n, out[4i..4i+3] = Philox(counter
+ * ctr[4i..4i+3], key) (host arrays).  With use_curand != 0 the same words come
+ * from cuRAND's Philox4_32_10 device generator started at that counter. */
+gpumcd_status gpumcd_debug_philox(gpumcd_ctx *ctx, const uint32_t *ctr, const uint32_t key[2],
+                                  uint64_t n, int32_t use_curand, uint32_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

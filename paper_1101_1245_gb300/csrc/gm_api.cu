@@ -1,0 +1,868 @@
+// C ABI of the gpumcd library (include/gpumcd.h): contexts, device memory
+// under an HBM budget, phantoms, plans and the launch sequence of the
+// persistent transport kernel.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "gm_common.cuh"
+#include "gm_host.h"
+
+using namespace gm;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Phantom {
+    int32_t dims[3];
+    double voxel[3];
+    uint64_t nvox;
+    DevBuf vox;     // packed voxel words
+    DevBuf rhomax;  // [NMAT] float bits
+    DevBuf maj;     // [2G] majorants
+};
+
+struct Plan {
+    int32_t phantom;
+    int32_t particle, beam;
+    double energy, cx, cy, field;
+    int32_t n_spec;
+    uint64_t seed;
+    uint32_t W;
+    uint64_t hist_done;
+    DevBuf tally;   // [W][nvox] u64
+    DevBuf ledger;  // [4] u64
+    DevBuf spec;    // [2(n_spec+1)] floats
+    gpumcd_run_stats acc;  // counters accumulated over the plan's runs
+};
+
+// Device control block of a launch sequence.
+struct Control {
+    unsigned long long prim_cursor[2];
+    unsigned long long qcur[2][2];  // [buffer][type]
+    unsigned long long counters[CNT_N];
+    int32_t error;
+    int32_t pad;
+};
+
+}  // namespace
+
+struct gpumcd_ctx {
+    int device = 0;
+    int n_sm = 0;
+    cudaStream_t stream = nullptr;
+    uint64_t budget = 0, used = 0;
+    bool tables = false;
+    int n_mat = 0;
+    gpumcd_physics phys{};
+    TableGeom geom{};
+    Phys dphys{};
+    DevBuf tab;
+    std::map<int32_t, Phantom> phantoms;
+    std::map<int32_t, Plan> plans;
+    int32_t next_id = 1;
+    gpumcd_launch launch{};
+    // scratch of the launch sequence
+    DevBuf stacks, queue[2][2], control, plandev, fold_tmp;
+    size_t fold_nvox = 0;
+    Control *h_control = nullptr;  // pinned
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool configured = false;
+};
+
+namespace {
+
+gpumcd_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return GPUMCD_OK;
+    if (e == cudaErrorMemoryAllocation) return GPUMCD_ERR_OOM;
+    return GPUMCD_ERR_CUDA;
+}
+
+#define CK(call)                                          \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_status(e_);    \
+    } while (0)
+
+#define ST(call)                                  \
+    do {                                          \
+        gpumcd_status s_ = (call);                \
+        if (s_ != GPUMCD_OK) return s_;           \
+    } while (0)
+
+gpumcd_status dev_alloc(gpumcd_ctx *c, DevBuf &b, size_t bytes) {
+    if (b.p && b.bytes >= bytes) return GPUMCD_OK;
+    size_t freed = b.bytes;
+    if (c->budget && c->used - freed + bytes > c->budget) return GPUMCD_ERR_BUDGET;
+    if (b.p) {
+        cudaFree(b.p);
+        c->used -= b.bytes;
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    if (bytes == 0) return GPUMCD_OK;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return GPUMCD_ERR_OOM;
+    }
+    b.bytes = bytes;
+    c->used += bytes;
+    return GPUMCD_OK;
+}
+
+void dev_free(gpumcd_ctx *c, DevBuf &b) {
+    if (b.p) {
+        cudaFree(b.p);
+        c->used -= b.bytes;
+    }
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+cudaStream_t pick(gpumcd_ctx *c, void *stream) { return stream ? (cudaStream_t)stream : c->stream; }
+
+gpumcd_status set_device(gpumcd_ctx *c) {
+    CK(cudaSetDevice(c->device));
+    return GPUMCD_OK;
+}
+
+bool valid_source(const gpumcd_ctx *c, const gpumcd_source *s) {
+    if (!s) return false;
+    if (s->particle != GPUMCD_PHOTON && s->particle != GPUMCD_ELECTRON) return false;
+    if (s->beam != GPUMCD_BEAM_PENCIL && s->beam != GPUMCD_BEAM_SQUARE) return false;
+    if (!std::isfinite(s->center_cm[0]) || !std::isfinite(s->center_cm[1])) return false;
+    if (s->beam == GPUMCD_BEAM_SQUARE && !(s->field_cm >= 0.0 && std::isfinite(s->field_cm))) return false;
+    if (s->n_spectrum < 0 || s->n_spectrum > GPUMCD_MAX_SPECTRUM_BINS) return false;
+    if (s->n_spectrum == 0) return s->energy_mev > 0.0 && s->energy_mev <= c->phys.e_max;
+    if (!s->spectrum_edges || !s->spectrum_weights) return false;
+    double tot = 0.0;
+    for (int i = 0; i < s->n_spectrum; ++i) {
+        if (!(s->spectrum_edges[i + 1] > s->spectrum_edges[i])) return false;
+        if (!(s->spectrum_weights[i] >= 0.0)) return false;
+        tot += s->spectrum_weights[i];
+    }
+    return tot > 0.0 && s->spectrum_edges[0] > 0.0 && s->spectrum_edges[s->n_spectrum] <= c->phys.e_max;
+}
+
+gpumcd_status ensure_scratch(gpumcd_ctx *c, int grid, int block) {
+    const size_t warps = (size_t)grid * (block / 32);
+    ST(dev_alloc(c, c->stacks, warps * 2 * c->launch.stack_capacity * sizeof(Rec)));
+    for (int b = 0; b < 2; ++b)
+        for (int t = 0; t < 2; ++t)
+            ST(dev_alloc(c, c->queue[b][t], (size_t)c->launch.overflow_capacity * sizeof(Rec)));
+    ST(dev_alloc(c, c->control, sizeof(Control)));
+    ST(dev_alloc(c, c->plandev, sizeof(PlanDev) * GPUMCD_MAX_PLANS_PER_RUN));
+    if (!c->h_control) CK(cudaMallocHost(&c->h_control, sizeof(Control)));
+    if (!c->configured) {
+        CK(transport_configure(block));
+        c->configured = true;
+    }
+    return GPUMCD_OK;
+}
+
+}  // namespace
+
+namespace gm {
+Grid make_grid(const TableGeom &g) {
+    const double ln2 = std::log(2.0), lq = std::log(kQ);
+    const double dp = (std::log(g.p1) - std::log(g.p0)) / (G - 1);
+    const double de = (std::log(g.e1) - std::log(g.e0)) / (G - 1);
+    const double dm = (std::log(MS_G_MAX) - std::log(MS_G_MIN)) / (G_MS - 1);
+    Grid r;
+    r.ph_a = (float)(ln2 / dp);
+    r.ph_bq = (float)((lq - std::log(g.p0)) / dp);
+    r.el_a = (float)(ln2 / de);
+    r.el_bq = (float)((lq - std::log(g.e0)) / de);
+    r.el_bm = (float)(-std::log(g.e0) / de);
+    r.ms_a = (float)(ln2 / dm);
+    r.ms_b = (float)(-std::log(MS_G_MIN) / dm);
+    return r;
+}
+}  // namespace gm
+
+extern "C" {
+
+const char *gpumcd_status_string(gpumcd_status s) {
+    switch (s) {
+        case GPUMCD_OK: return "ok";
+        case GPUMCD_ERR_INVALID_ARG: return "invalid argument";
+        case GPUMCD_ERR_OOM: return "device out of memory";
+        case GPUMCD_ERR_CUDA: return "CUDA error";
+        case GPUMCD_ERR_QUEUE_OVERFLOW: return "particle queue overflow";
+        case GPUMCD_ERR_TIMEOUT: return "device wait timed out";
+        case GPUMCD_ERR_NOT_FOUND: return "unknown id";
+        case GPUMCD_ERR_BUDGET: return "HBM budget exceeded";
+        case GPUMCD_ERR_STATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+gpumcd_status gpumcd_init(gpumcd_ctx **out, int32_t device, uint64_t hbm_budget_bytes) {
+    if (!out) return GPUMCD_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return GPUMCD_ERR_CUDA;
+    }
+    if (device < 0 || device >= n) return GPUMCD_ERR_INVALID_ARG;
+    gpumcd_ctx *c = new gpumcd_ctx();
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_status(e);
+    }
+    c->launch.block_threads = 512;
+    c->launch.blocks_per_sm = 1;
+    c->launch.stack_capacity = 256;
+    c->launch.switch_high = 128;
+    c->launch.refill_low = 16;
+    c->launch.chunk = 64;
+    c->launch.overflow_capacity = 1u << 20;
+    c->launch.flags = 0;
+    *out = c;
+    return GPUMCD_OK;
+}
+
+gpumcd_status gpumcd_destroy(gpumcd_ctx *c) {
+    if (!c) return GPUMCD_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto &kv : c->plans) {
+        dev_free(c, kv.second.tally);
+        dev_free(c, kv.second.ledger);
+        dev_free(c, kv.second.spec);
+    }
+    for (auto &kv : c->phantoms) {
+        dev_free(c, kv.second.vox);
+        dev_free(c, kv.second.rhomax);
+        dev_free(c, kv.second.maj);
+    }
+    dev_free(c, c->tab);
+    dev_free(c, c->stacks);
+    for (int b = 0; b < 2; ++b)
+        for (int t = 0; t < 2; ++t) dev_free(c, c->queue[b][t]);
+    dev_free(c, c->control);
+    dev_free(c, c->plandev);
+    dev_free(c, c->fold_tmp);
+    if (c->h_control) cudaFreeHost(c->h_control);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return GPUMCD_OK;
+}
+
+gpumcd_status gpumcd_load_materials(gpumcd_ctx *c, const gpumcd_material *mats, int32_t n,
+                                    const gpumcd_physics *ph) {
+    if (!c || !mats || !ph || n < 1 || n > GPUMCD_MAX_MATERIALS) return GPUMCD_ERR_INVALID_ARG;
+    if (!c->phantoms.empty() || !c->plans.empty()) return GPUMCD_ERR_STATE;
+    if (!(ph->p_cut > 0 && ph->e_abs > 0 && ph->t_c > 0 && ph->k_c > 0 && ph->estepe > 0 &&
+          ph->estepe <= 1.0 && ph->e_max > ph->e_abs && ph->e_max > ph->p_cut && ph->e_max <= 20.0 &&
+          ph->nudge_cm >= 0 && ph->nudge_cm < 1.0))
+        return GPUMCD_ERR_INVALID_ARG;
+    for (int m = 0; m < n; ++m) {
+        const gpumcd_material &M = mats[m];
+        if (M.n_elements < 1 || M.n_elements > GPUMCD_MAX_ELEMENTS || !(M.I_eV > 0)) return GPUMCD_ERR_INVALID_ARG;
+        double ws = 0;
+        for (int j = 0; j < M.n_elements; ++j) {
+            if (M.Z[j] < 1 || M.Z[j] > 100 || !(M.A[j] > 0) || !(M.w[j] >= 0)) return GPUMCD_ERR_INVALID_ARG;
+            ws += M.w[j];
+        }
+        if (!(ws > 0)) return GPUMCD_ERR_INVALID_ARG;
+    }
+    ST(set_device(c));
+    ST(dev_alloc(c, c->tab, TAB_BYTES));
+    c->phys = *ph;
+    c->n_mat = n;
+    c->geom.p0 = 0.5 * ph->p_cut;
+    c->geom.p1 = ph->e_max * 1.0001;
+    c->geom.e0 = 0.25 * std::fmin(ph->e_abs, ph->t_c);
+    c->geom.e1 = ph->e_max * 1.0001;
+    c->dphys.p_cut_q = (uint32_t)std::llround(ph->p_cut / kQ);
+    c->dphys.e_abs_q = (uint32_t)std::llround(ph->e_abs / kQ);
+    c->dphys.two_mc2_q = (uint32_t)std::llround(2.0 * kMC2 / kQ);
+    c->dphys.t_c = (float)ph->t_c;
+    c->dphys.k_c = (float)ph->k_c;
+    c->dphys.estepe = (float)ph->estepe;
+    c->dphys.nudge = (float)ph->nudge_cm;
+    c->dphys.grid = make_grid(c->geom);
+    CK(cudaMemsetAsync(c->tab.p, 0, TAB_BYTES, c->stream));
+    CK(launch_build_tables(mats, n, c->geom, ph->t_c, ph->k_c, (float *)c->tab.p, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->tables = true;
+    return GPUMCD_OK;
+}
+
+static gpumcd_status create_phantom_impl(gpumcd_ctx *c, const int32_t dims[3], const double voxel[3],
+                                         const uint8_t *mat, const float *rho, bool device,
+                                         cudaStream_t s, int32_t *id) {
+    if (!c || !dims || !voxel || !mat || !rho || !id) return GPUMCD_ERR_INVALID_ARG;
+    if (!c->tables) return GPUMCD_ERR_STATE;
+    for (int a = 0; a < 3; ++a) {
+        if (dims[a] < 1 || dims[a] > 4096) return GPUMCD_ERR_INVALID_ARG;
+        if (!(voxel[a] > 0.0) || !std::isfinite(voxel[a])) return GPUMCD_ERR_INVALID_ARG;
+    }
+    const uint64_t nvox = (uint64_t)dims[0] * dims[1] * dims[2];
+    if (nvox >= (1ull << 32)) return GPUMCD_ERR_INVALID_ARG;
+    ST(set_device(c));
+    Phantom ph{};
+    for (int a = 0; a < 3; ++a) {
+        ph.dims[a] = dims[a];
+        ph.voxel[a] = voxel[a];
+    }
+    ph.nvox = nvox;
+    gpumcd_status st = dev_alloc(c, ph.vox, nvox * 4);
+    if (st == GPUMCD_OK) st = dev_alloc(c, ph.rhomax, 16 * 4);
+    if (st == GPUMCD_OK) st = dev_alloc(c, ph.maj, MAJ_FLOATS * 4);
+    DevBuf tmp_mat, tmp_rho, bad;
+    if (st == GPUMCD_OK && !device) st = dev_alloc(c, tmp_mat, nvox);
+    if (st == GPUMCD_OK && !device) st = dev_alloc(c, tmp_rho, nvox * 4);
+    if (st == GPUMCD_OK) st = dev_alloc(c, bad, 4);
+    cudaError_t e = cudaSuccess;
+    int h_bad = 0;
+    if (st == GPUMCD_OK) {
+        const uint8_t *dm = mat;
+        const float *dr = rho;
+        if (!device) {
+            e = cudaMemcpyAsync(tmp_mat.p, mat, nvox, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(tmp_rho.p, rho, nvox * 4, cudaMemcpyHostToDevice, s);
+            dm = (const uint8_t *)tmp_mat.p;
+            dr = (const float *)tmp_rho.p;
+        }
+        if (e == cudaSuccess) e = cudaMemsetAsync(ph.rhomax.p, 0, 16 * 4, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(bad.p, 0, 4, s);
+        if (e == cudaSuccess)
+            e = launch_pack_phantom(dm, dr, nvox, c->n_mat, (uint32_t *)ph.vox.p, (unsigned int *)ph.rhomax.p,
+                                    (int *)bad.p, s);
+        if (e == cudaSuccess)
+            e = launch_majorants((const float *)c->tab.p, (const unsigned int *)ph.rhomax.p, c->n_mat,
+                                 (float *)ph.maj.p, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, bad.p, 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_status(e);
+        else if (h_bad) st = GPUMCD_ERR_INVALID_ARG;
+    }
+    dev_free(c, tmp_mat);
+    dev_free(c, tmp_rho);
+    dev_free(c, bad);
+    if (st != GPUMCD_OK) {
+        dev_free(c, ph.vox);
+        dev_free(c, ph.rhomax);
+        dev_free(c, ph.maj);
+        return st;
+    }
+    *id = c->next_id++;
+    c->phantoms[*id] = ph;
+    return GPUMCD_OK;
+}
+
+gpumcd_status gpumcd_create_phantom(gpumcd_ctx *c, const int32_t dims[3], const double voxel_cm[3],
+                                    const uint8_t *material_ids, const float *densities, int32_t *id) {
+    if (!c) return GPUMCD_ERR_INVALID_ARG;
+    return create_phantom_impl(c, dims, voxel_cm, material_ids, densities, false, c->stream, id);
+}
+
+gpumcd_status gpumcd_create_phantom_device(gpumcd_ctx *c, const int32_t dims[3], const double voxel_cm[3],
+                                           const uint8_t *material_ids, const float *densities, void *stream,
+                                           int32_t *id) {
+    if (!c) return GPUMCD_ERR_INVALID_ARG;
+    return create_phantom_impl(c, dims, voxel_cm, material_ids, densities, true, pick(c, stream), id);
+}
+
+gpumcd_status gpumcd_destroy_phantom(gpumcd_ctx *c, int32_t id) {
+    if (!c) return GPUMCD_ERR_INVALID_ARG;
+    auto it = c->phantoms.find(id);
+    if (it == c->phantoms.end()) return GPUMCD_ERR_NOT_FOUND;
+    for (auto &kv : c->plans)
+        if (kv.second.phantom == id) return GPUMCD_ERR_STATE;
+    ST(set_device(c));
+    cudaStreamSynchronize(c->stream);
+    dev_free(c, it->second.vox);
+    dev_free(c, it->second.rhomax);
+    dev_free(c, it->second.maj);
+    c->phantoms.erase(it);
+    return GPUMCD_OK;
+}
+
+gpumcd_status gpumcd_plan_open(gpumcd_ctx *c, int32_t phantom_id, const gpumcd_source *src, uint64_t seed,
+                               uint32_t n_batches, int32_t *plan_id) {
+    if (!c || !plan_id) return GPUMCD_ERR_INVALID_ARG;
+    if (!c->tables) return GPUMCD_ERR_STATE;
+    auto it = c->phantoms.find(phantom_id);
+    if (it == c->phantoms.end()) return GPUMCD_ERR_NOT_FOUND;
+    if (!valid_source(c, src)) return GPUMCD_ERR_INVALID_ARG;
+    if (n_batches == 0) n_batches = 32;
+    if (n_batches < 8 || n_batches > 64 || (n_batches & (n_batches - 1))) return GPUMCD_ERR_INVALID_ARG;
+    ST(set_device(c));
+    Plan p{};
+    p.phantom = phantom_id;
+    p.particle = src->particle;
+    p.beam = src->beam;
+    p.energy = src->energy_mev;
+    p.cx = src->center_cm[0];
+    p.cy = src->center_cm[1];
+    p.field = src->field_cm;
+    p.n_spec = src->n_spectrum;
+    p.seed = seed;
+    p.W = n_batches;
+    const uint64_t nvox = it->second.nvox;
+    gpumcd_status st = dev_alloc(c, p.tally, (size_t)n_batches * nvox * 8);
+    if (st == GPUMCD_OK) st = dev_alloc(c, p.ledger, 4 * 8);
+    DevBuf tmp;
+    if (st == GPUMCD_OK && p.n_spec > 0) {
+        st = dev_alloc(c, p.spec, (size_t)2 * (p.n_spec + 1) * 4);
+        if (st == GPUMCD_OK) st = dev_alloc(c, tmp, (size_t)(2 * p.n_spec + 1) * 8);
+        if (st == GPUMCD_OK) {
+            double *d = (double *)tmp.p;
+            cudaError_t e = cudaMemcpyAsync(d, src->spectrum_edges, (p.n_spec + 1) * 8, cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(d + p.n_spec + 1, src->spectrum_weights, p.n_spec * 8, cudaMemcpyHostToDevice,
+                                    c->stream);
+            if (e == cudaSuccess) e = launch_spectrum(d, d + p.n_spec + 1, p.n_spec, (float *)p.spec.p, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) st = cuda_status(e);
+        }
+    }
+    dev_free(c, tmp);
+    if (st == GPUMCD_OK) {
+        cudaError_t e = cudaMemsetAsync(p.tally.p, 0, p.tally.bytes, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p.ledger.p, 0, p.ledger.bytes, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) st = cuda_status(e);
+    }
+    if (st != GPUMCD_OK) {
+        dev_free(c, p.tally);
+        dev_free(c, p.ledger);
+        dev_free(c, p.spec);
+        return st;
+    }
+    *plan_id = c->next_id++;
+    c->plans[*plan_id] = p;
+    return GPUMCD_OK;
+}
+
+gpumcd_status gpumcd_plan_close(gpumcd_ctx *c, int32_t plan_id) {
+    if (!c) return GPUMCD_ERR_INVALID_ARG;
+    auto it = c->plans.find(plan_id);
+    if (it == c->plans.end()) return GPUMCD_ERR_NOT_FOUND;
+    ST(set_device(c));
+    cudaStreamSynchronize(c->stream);
+    dev_free(c, it->second.tally);
+    dev_free(c, it->second.ledger);
+    dev_free(c, it->second.spec);
+    c->plans.erase(it);
+    return GPUMCD_OK;
+}
+
+gpumcd_status gpumcd_plan_reset(gpumcd_ctx *c, int32_t plan_id, uint64_t seed, void *stream) {
+    if (!c) return GPUMCD_ERR_INVALID_ARG;
+    auto it = c->plans.find(plan_id);
+    if (it == c->plans.end()) return GPUMCD_ERR_NOT_FOUND;
+    ST(set_device(c));
+    cudaStream_t s = pick(c, stream);
+    Plan &p = it->second;
+    CK(cudaMemsetAsync(p.tally.p, 0, p.tally.bytes, s));
+    CK(cudaMemsetAsync(p.ledger.p, 0, p.ledger.bytes, s));
+    p.seed = seed;
+    p.hist_done = 0;
+    p.acc = gpumcd_run_stats{};
+    return GPUMCD_OK;
+}
+
+gpumcd_status gpumcd_plan_histories(gpumcd_ctx *c, int32_t plan_id, uint64_t *h) {
+    if (!c || !h) return GPUMCD_ERR_INVALID_ARG;
+    auto it = c->plans.find(plan_id);
+    if (it == c->plans.end()) return GPUMCD_ERR_NOT_FOUND;
+    *h = it->second.hist_done;
+    return GPUMCD_OK;
+}
+
+gpumcd_status gpumcd_run(gpumcd_ctx *c, int32_t n_plans, const int32_t *ids, const uint64_t *n_hist, void *stream) {
+    if (!c || n_plans < 1 || n_plans > GPUMCD_MAX_PLANS_PER_RUN || !ids || !n_hist) return GPUMCD_ERR_INVALID_ARG;
+    if (!c->tables) return GPUMCD_ERR_STATE;
+    std::vector<Plan *> pl(n_plans);
+    for (int i = 0; i < n_plans; ++i) {
+        auto it = c->plans.find(ids[i]);
+        if (it == c->plans.end()) return GPUMCD_ERR_NOT_FOUND;
+        for (int j = 0; j < i; ++j)
+            if (ids[j] == ids[i]) return GPUMCD_ERR_INVALID_ARG;
+        pl[i] = &it->second;
+        if (pl[i]->hist_done + n_hist[i] > (1ull << 32)) return GPUMCD_ERR_INVALID_ARG;
+    }
+    ST(set_device(c));
+    cudaStream_t s = pick(c, stream);
+    const int block = (int)c->launch.block_threads;
+    const int grid = c->n_sm * (int)c->launch.blocks_per_sm;
+    ST(ensure_scratch(c, grid, block));
+
+    std::vector<PlanDev> pd(n_plans);
+    TransportArgs A;
+    memset(&A, 0, sizeof A);
+    for (int i = 0; i < n_plans; ++i) {
+        const Plan &p = *pl[i];
+        const Phantom &ph = c->phantoms.at(p.phantom);
+        PlanDev &d = pd[i];
+        memset(&d, 0, sizeof d);
+        d.vox = (const uint32_t *)ph.vox.p;
+        d.tally = (unsigned long long *)p.tally.p;
+        d.ledger = (unsigned long long *)p.ledger.p;
+        d.maj = (const float *)ph.maj.p;
+        d.spec = (const float *)p.spec.p;
+        d.nx = ph.dims[0];
+        d.ny = ph.dims[1];
+        d.nz = ph.dims[2];
+        d.n_spec = p.n_spec;
+        d.dx = (float)ph.voxel[0];
+        d.dy = (float)ph.voxel[1];
+        d.dz = (float)ph.voxel[2];
+        d.inv_dx = (float)(1.0 / ph.voxel[0]);
+        d.inv_dy = (float)(1.0 / ph.voxel[1]);
+        d.inv_dz = (float)(1.0 / ph.voxel[2]);
+        d.X = (float)(ph.dims[0] * ph.voxel[0]);
+        d.Y = (float)(ph.dims[1] * ph.voxel[1]);
+        d.Z = (float)(ph.dims[2] * ph.voxel[2]);
+        d.cx = (float)p.cx;
+        d.cy = (float)p.cy;
+        d.field = (float)p.field;
+        d.nvox = (uint32_t)ph.nvox;
+        d.bmask = p.W - 1;
+        d.key_lo = (uint32_t)p.seed;
+        d.key_hi = (uint32_t)(p.seed >> 32);
+        d.src_type = p.particle;
+        d.beam = p.beam;
+        d.e_src_q = (uint32_t)std::llround(p.energy / kQ);
+        d.hist_base = p.hist_done;
+        d.n_hist = n_hist[i];
+        const int t = p.particle;
+        A.prim_plan[t][A.n_prim_plans[t]] = (uint8_t)i;
+        A.prim_off[t][A.n_prim_plans[t] + 1] = A.prim_off[t][A.n_prim_plans[t]] + n_hist[i];
+        A.n_prim_plans[t]++;
+    }
+    Control *dc = (Control *)c->control.p;
+    A.tables = (const float *)c->tab.p;
+    A.phys = c->dphys;
+    A.plans = (const PlanDev *)c->plandev.p;
+    A.n_plans = n_plans;
+    A.prim_cursor = dc->prim_cursor;
+    A.stacks = (Rec *)c->stacks.p;
+    A.stack_cap = c->launch.stack_capacity;
+    A.switch_high = c->launch.switch_high;
+    A.refill_low = c->launch.refill_low;
+    A.chunk = c->launch.chunk;
+    A.flags = c->launch.flags;
+    A.counters = dc->counters;
+    A.error = &dc->error;
+    CK(cudaMemcpyAsync(c->plandev.p, pd.data(), sizeof(PlanDev) * n_plans, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(dc, 0, sizeof(Control), s));
+    CK(cudaEventRecord(c->ev0, s));
+    gpumcd_status result = GPUMCD_OK;
+    uint32_t launches = 0;
+    unsigned long long in_count[2] = {0, 0};
+    for (int k = 0; k < 1000; ++k) {
+        const int bi = k & 1, bo = bi ^ 1;
+        for (int t = 0; t < 2; ++t) {
+            A.in[t].rec = (Rec *)c->queue[bi][t].p;
+            A.in[t].cursor = &dc->qcur[bi][t];
+            A.in[t].capacity = c->launch.overflow_capacity;
+            A.out[t].rec = (Rec *)c->queue[bo][t].p;
+            A.out[t].cursor = &dc->qcur[bo][t];
+            A.out[t].capacity = c->launch.overflow_capacity;
+            A.in_count[t] = in_count[t];
+        }
+        CK(cudaMemsetAsync(dc->qcur[bo], 0, sizeof(dc->qcur[bo]), s));
+        CK(launch_transport(A, grid, block, s));
+        ++launches;
+        CK(cudaMemcpyAsync(c->h_control, dc, sizeof(Control), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (c->h_control->error != 0) {
+            result = c->h_control->error;
+            break;
+        }
+        const unsigned long long o0 = c->h_control->qcur[bo][0], o1 = c->h_control->qcur[bo][1];
+        if (o0 == 0 && o1 == 0) break;
+        in_count[0] = o0 < c->launch.overflow_capacity ? o0 : c->launch.overflow_capacity;
+        in_count[1] = o1 < c->launch.overflow_capacity ? o1 : c->launch.overflow_capacity;
+        // this launch's output becomes the next launch's input: restart its cursor
+        CK(cudaMemsetAsync(dc->qcur[bo], 0, sizeof(dc->qcur[bo]), s));
+        if (k == 999) result = GPUMCD_ERR_TIMEOUT;
+    }
+    CK(cudaEventRecord(c->ev1, s));
+    CK(cudaEventSynchronize(c->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    const Control &hc = *c->h_control;
+    for (int i = 0; i < n_plans; ++i) {
+        Plan &p = *pl[i];
+        if (result == GPUMCD_OK) p.hist_done += n_hist[i];
+        p.acc.n_launches += launches;
+        p.acc.transport_ms += ms;
+    }
+    // run-wide counters go to every plan of a single-plan run and to the first plan otherwise
+    Plan &p0 = *pl[0];
+    p0.acc.n_photon_events += hc.counters[CNT_PH_EVENTS];
+    p0.acc.n_photon_real += hc.counters[CNT_PH_REAL];
+    p0.acc.n_compton += hc.counters[CNT_COMPTON];
+    p0.acc.n_photo += hc.counters[CNT_PHOTO];
+    p0.acc.n_pair += hc.counters[CNT_PAIR];
+    p0.acc.n_electron_steps += hc.counters[CNT_E_STEPS];
+    p0.acc.n_hard_real += hc.counters[CNT_HARD_REAL];
+    p0.acc.n_hard_fict += hc.counters[CNT_HARD_FICT];
+    p0.acc.n_moller += hc.counters[CNT_MOLLER];
+    p0.acc.n_brem += hc.counters[CNT_BREM];
+    p0.acc.n_photons += hc.counters[CNT_PHOTONS];
+    p0.acc.n_electrons += hc.counters[CNT_ELECTRONS];
+    p0.acc.n_overflow += hc.counters[CNT_OVERFLOW];
+    p0.acc.n_spilled += hc.counters[CNT_SPILLS];
+    p0.acc.n_sampler_capped += hc.counters[CNT_SAMPLER_CAP];
+    return result;
+}
+
+gpumcd_status gpumcd_plan_result(gpumcd_ctx *c, int32_t plan_id, double thr, double *dose, double *sigma,
+                                 void *stream, gpumcd_run_stats *stats) {
+    if (!c) return GPUMCD_ERR_INVALID_ARG;
+    auto it = c->plans.find(plan_id);
+    if (it == c->plans.end()) return GPUMCD_ERR_NOT_FOUND;
+    if (!(thr >= 0.0 && thr <= 1.0)) return GPUMCD_ERR_INVALID_ARG;
+    ST(set_device(c));
+    cudaStream_t s = pick(c, stream);
+    Plan &p = it->second;
+    const Phantom &ph = c->phantoms.at(p.phantom);
+    const uint64_t nvox = ph.nvox;
+    // scratch: [dose | sigma] when the caller passes NULL, then [n_b (64) | dmax | sum | count | esum]
+    const size_t need = (size_t)nvox * 16 + 64 * 8 + 64;
+    ST(dev_alloc(c, c->fold_tmp, need));
+    double *tdose = (double *)c->fold_tmp.p;
+    double *tsig = tdose + nvox;
+    double *nb = tsig + nvox;
+    unsigned long long *red = (unsigned long long *)(nb + 64);
+    double *ddose = dose ? dose : tdose;
+    double *dsig = sigma ? sigma : tsig;
+    double h_nb[64] = {0};
+    const uint64_t N = p.hist_done;
+    const uint64_t cyc = 32ull * p.W;
+    for (uint32_t b = 0; b < p.W; ++b) {
+        const uint64_t full = N / cyc, rem = N % cyc;
+        uint64_t extra = rem > 32ull * b ? rem - 32ull * b : 0;
+        if (extra > 32) extra = 32;
+        h_nb[b] = (double)(32ull * full + extra);
+    }
+    CK(cudaMemsetAsync(red, 0, 64, s));
+    const double inv_vol = 1.0 / (ph.voxel[0] * ph.voxel[1] * ph.voxel[2]);
+    if (N > 0) {
+        CK(launch_fold((const unsigned long long *)p.tally.p, (const uint32_t *)ph.vox.p, nvox, (int)p.W, h_nb,
+                       (double)N, inv_vol, ddose, dsig, red, red + 3, c->n_sm, s));
+        CK(launch_sthr(ddose, dsig, nvox, red, thr, (double *)(red + 1), red + 2, c->n_sm, s));
+    } else {
+        CK(cudaMemsetAsync(ddose, 0, nvox * 8, s));
+        CK(cudaMemsetAsync(dsig, 0, nvox * 8, s));
+    }
+    unsigned long long h_red[4], h_led[4];
+    CK(cudaMemcpyAsync(h_red, red, sizeof h_red, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h_led, p.ledger.p, sizeof h_led, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (stats) {
+        *stats = p.acc;
+        stats->histories = N;
+        stats->n_batches = p.W;
+        stats->e_incident = h_led[0];
+        stats->e_escaped = h_led[1];
+        stats->e_rest = h_led[2];
+        stats->e_deposited = h_red[3];
+        double dm;
+        memcpy(&dm, &h_red[0], 8);
+        stats->d_max_gy = dm;
+        double ssum;
+        memcpy(&ssum, &h_red[1], 8);
+        stats->s_thr = h_red[2] ? ssum / (double)h_red[2] : 0.0;
+    }
+    return GPUMCD_OK;
+}
+
+static gpumcd_status simulate_impl(gpumcd_ctx *c, int32_t phantom_id, const gpumcd_source *src, uint64_t n,
+                                   uint64_t seed, double target, double *dose, double *sigma, bool host,
+                                   cudaStream_t s, gpumcd_run_stats *stats) {
+    if (!c || n == 0 || !(target >= 0.0)) return GPUMCD_ERR_INVALID_ARG;
+    int32_t pid = 0;
+    ST(gpumcd_plan_open(c, phantom_id, src, seed, 32, &pid));
+    gpumcd_status st = GPUMCD_OK;
+    gpumcd_run_stats rs{};
+    const uint64_t cap = target > 0.0 ? std::max<uint64_t>(16 * n, 1000000000ull) : n;
+    uint64_t done = 0;
+    do {
+        st = gpumcd_run(c, 1, &pid, &n, s);
+        if (st != GPUMCD_OK) break;
+        done += n;
+        if (target <= 0.0) break;
+        st = gpumcd_plan_result(c, pid, 0.5, nullptr, nullptr, s, &rs);
+        if (st != GPUMCD_OK) break;
+    } while (rs.s_thr > target && done + n <= cap);
+    const uint64_t nvox = c->phantoms.at(phantom_id).nvox;
+    if (st == GPUMCD_OK) {
+        if (host) {
+            st = gpumcd_plan_result(c, pid, 0.5, nullptr, nullptr, s, &rs);
+            if (st == GPUMCD_OK) {
+                const double *td = (const double *)c->fold_tmp.p;
+                cudaError_t e = cudaSuccess;
+                if (dose) e = cudaMemcpyAsync(dose, td, nvox * 8, cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess && sigma) e = cudaMemcpyAsync(sigma, td + nvox, nvox * 8, cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess) st = cuda_status(e);
+            }
+        } else {
+            st = gpumcd_plan_result(c, pid, 0.5, dose, sigma, s, &rs);
+        }
+    }
+    if (st == GPUMCD_OK && stats) *stats = rs;
+    gpumcd_plan_close(c, pid);
+    return st;
+}
+
+gpumcd_status gpumcd_simulate(gpumcd_ctx *c, int32_t phantom_id, const gpumcd_source *src, uint64_t n,
+                              uint64_t seed, double target, double *dose, double *sigma, gpumcd_run_stats *stats) {
+    if (!c) return GPUMCD_ERR_INVALID_ARG;
+    return simulate_impl(c, phantom_id, src, n, seed, target, dose, sigma, true, c->stream, stats);
+}
+
+gpumcd_status gpumcd_simulate_device(gpumcd_ctx *c, int32_t phantom_id, const gpumcd_source *src, uint64_t n,
+                                     uint64_t seed, double target, double *dose, double *sigma, void *stream,
+                                     gpumcd_run_stats *stats) {
+    if (!c) return GPUMCD_ERR_INVALID_ARG;
+    return simulate_impl(c, phantom_id, src, n, seed, target, dose, sigma, false, pick(c, stream), stats);
+}
+
+gpumcd_status gpumcd_memory(gpumcd_ctx *c, uint64_t *used, uint64_t *budget) {
+    if (!c || !used || !budget) return GPUMCD_ERR_INVALID_ARG;
+    *used = c->used;
+    *budget = c->budget;
+    return GPUMCD_OK;
+}
+
+gpumcd_status gpumcd_set_launch(gpumcd_ctx *c, const gpumcd_launch *l) {
+    if (!c || !l) return GPUMCD_ERR_INVALID_ARG;
+    gpumcd_launch n = c->launch;
+    if (l->block_threads) n.block_threads = l->block_threads;
+    if (l->blocks_per_sm) n.blocks_per_sm = l->blocks_per_sm;
+    if (l->stack_capacity) n.stack_capacity = l->stack_capacity;
+    if (l->switch_high) n.switch_high = l->switch_high;
+    if (l->refill_low) n.refill_low = l->refill_low;
+    if (l->chunk) n.chunk = l->chunk;
+    if (l->overflow_capacity) n.overflow_capacity = l->overflow_capacity;
+    n.flags = l->flags;
+    if (n.block_threads % 32 || n.block_threads < 32 || n.block_threads > 512) return GPUMCD_ERR_INVALID_ARG;
+    if (n.blocks_per_sm < 1 || n.blocks_per_sm > 3) return GPUMCD_ERR_INVALID_ARG;
+    if (n.stack_capacity < 128 || n.stack_capacity > (1u << 16)) return GPUMCD_ERR_INVALID_ARG;
+    if (n.switch_high < 32 || n.switch_high > n.stack_capacity) return GPUMCD_ERR_INVALID_ARG;
+    if (n.refill_low > 32 || n.chunk < 1 || n.chunk > 4096) return GPUMCD_ERR_INVALID_ARG;
+    if (n.overflow_capacity < 64 || n.overflow_capacity > (1u << 26)) return GPUMCD_ERR_INVALID_ARG;
+    c->launch = n;
+    return GPUMCD_OK;
+}
+
+gpumcd_status gpumcd_get_launch(gpumcd_ctx *c, gpumcd_launch *l) {
+    if (!c || !l) return GPUMCD_ERR_INVALID_ARG;
+    *l = c->launch;
+    return GPUMCD_OK;
+}
+
+gpumcd_status gpumcd_get_tables(gpumcd_ctx *c, int32_t which, float *out, int32_t *count) {
+    if (!c || !count) return GPUMCD_ERR_INVALID_ARG;
+    if (!c->tables) return GPUMCD_ERR_STATE;
+    int off = 0, n = 0;
+    if (which == 0) { off = TAB_PH; n = NMAT * 3 * G; }
+    else if (which == 1) { off = TAB_EL; n = NMAT * 4 * G; }
+    else if (which == 2) { off = TAB_MS; n = G_MS; }
+    else if (which == 3) { n = 2 * G; }
+    else return GPUMCD_ERR_INVALID_ARG;
+    *count = n;
+    if (!out) return GPUMCD_OK;
+    ST(set_device(c));
+    if (which == 3) {
+        DevBuf tmp;
+        ST(dev_alloc(c, tmp, 2 * G * 4));
+        cudaError_t e = launch_grid_energies(c->geom, (float *)tmp.p, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp.p, 2 * G * 4, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        dev_free(c, tmp);
+        return cuda_status(e);
+    }
+    CK(cudaMemcpyAsync(out, (const float *)c->tab.p + off, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return GPUMCD_OK;
+}
+
+gpumcd_status gpumcd_debug_sample(gpumcd_ctx *c, int32_t kind, double p0, int32_t material,
+                                  const gpumcd_source *src, uint64_t n, uint64_t seed, float *out) {
+    if (!c || !out || n == 0 || n > (1ull << 28) || kind < 0 || kind > 6) return GPUMCD_ERR_INVALID_ARG;
+    if (!c->tables) return GPUMCD_ERR_STATE;
+    if (material < 0 || material >= c->n_mat) return GPUMCD_ERR_INVALID_ARG;
+    if (kind == 5 && (!valid_source(c, src) || src->n_spectrum < 1)) return GPUMCD_ERR_INVALID_ARG;
+    if (kind != 5 && !(p0 > 0.0)) return GPUMCD_ERR_INVALID_ARG;
+    if (kind == 2 && !(p0 > 2.0 * c->phys.t_c)) return GPUMCD_ERR_INVALID_ARG;
+    if (kind == 3 && !(p0 > c->phys.k_c)) return GPUMCD_ERR_INVALID_ARG;
+    ST(set_device(c));
+    DevBuf o, spec, tmp;
+    gpumcd_status st = dev_alloc(c, o, n * 4);
+    cudaError_t e = cudaSuccess;
+    int ns = 0;
+    if (st == GPUMCD_OK && kind == 5) {
+        ns = src->n_spectrum;
+        st = dev_alloc(c, spec, (size_t)2 * (ns + 1) * 4);
+        if (st == GPUMCD_OK) st = dev_alloc(c, tmp, (size_t)(2 * ns + 1) * 8);
+        if (st == GPUMCD_OK) {
+            double *d = (double *)tmp.p;
+            e = cudaMemcpyAsync(d, src->spectrum_edges, (ns + 1) * 8, cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(d + ns + 1, src->spectrum_weights, ns * 8, cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess) e = launch_spectrum(d, d + ns + 1, ns, (float *)spec.p, c->stream);
+        }
+    }
+    if (st == GPUMCD_OK && e == cudaSuccess)
+        e = launch_debug_sample((const float *)c->tab.p, c->dphys, kind, (float)p0, material,
+                                (const float *)spec.p, ns, n, seed, (float *)o.p, c->stream);
+    if (st == GPUMCD_OK && e == cudaSuccess) e = cudaMemcpyAsync(out, o.p, n * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (st == GPUMCD_OK && e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, o);
+    dev_free(c, spec);
+    dev_free(c, tmp);
+    if (st != GPUMCD_OK) return st;
+    return cuda_status(e);
+}
+
+gpumcd_status gpumcd_debug_philox(gpumcd_ctx *c, const uint32_t *ctr, const uint32_t key[2], uint64_t n,
+                                  int32_t use_curand, uint32_t *out) {
+    if (!c || !ctr || !key || !out || n == 0 || n > (1ull << 24)) return GPUMCD_ERR_INVALID_ARG;
+    ST(set_device(c));
+    DevBuf dc, dout;
+    gpumcd_status st = dev_alloc(c, dc, n * 16);
+    if (st == GPUMCD_OK) st = dev_alloc(c, dout, n * 16);
+    cudaError_t e = cudaSuccess;
+    if (st == GPUMCD_OK) {
+        e = cudaMemcpyAsync(dc.p, ctr, n * 16, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = launch_philox((const uint32_t *)dc.p, make_uint2(key[0], key[1]), n, use_curand, (uint32_t *)dout.p,
+                              c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout.p, n * 16, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    dev_free(c, dc);
+    dev_free(c, dout);
+    if (st != GPUMCD_OK) return st;
+    return cuda_status(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,46 @@
+// Host-side declarations shared by the gpumcd library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gm_common.cuh"
+
+namespace gm {
+
+// Energy bounds of the two table grids (MeV).
+struct TableGeom {
+    double p0, p1;  // photon grid
+    double e0, e1;  // electron grid
+};
+
+Grid make_grid(const TableGeom &g);
+
+cudaError_t launch_build_tables(const gpumcd_material *mats, int n_mat, const TableGeom &g,
+                                double t_c, double k_c, float *d_tab, cudaStream_t s);
+cudaError_t launch_grid_energies(const TableGeom &g, float *out, cudaStream_t s);
+cudaError_t launch_pack_phantom(const uint8_t *mat, const float *rho, uint64_t nvox, int n_mat,
+                                uint32_t *vox, unsigned int *rho_max_bits, int *bad, cudaStream_t s);
+cudaError_t launch_majorants(const float *tab, const unsigned int *rho_max_bits, int n_mat, float *maj,
+                             cudaStream_t s);
+cudaError_t launch_spectrum(const double *edges, const double *w, int n, float *out, cudaStream_t s);
+cudaError_t launch_fold(const unsigned long long *tally, const uint32_t *vox, uint64_t nvox, int W,
+                        const double *n_b, double n_tot, double inv_vol, double *dose, double *sigma,
+                        unsigned long long *dmax_bits, unsigned long long *dep_sum, int n_sm, cudaStream_t s);
+cudaError_t launch_sthr(const double *dose, const double *sigma, uint64_t nvox,
+                        const unsigned long long *dmax_bits, double thr, double *sum,
+                        unsigned long long *count, int n_sm, cudaStream_t s);
+cudaError_t launch_sum_u64(const unsigned long long *a, uint64_t n, unsigned long long *out, int n_sm,
+                           cudaStream_t s);
+cudaError_t launch_philox(const uint32_t *ctr, uint2 key, uint64_t n, int curand, uint32_t *out,
+                          cudaStream_t s);
+
+// Transport (gm_transport.cu).
+size_t transport_smem_bytes(int block_threads);
+cudaError_t transport_configure(int block_threads);
+cudaError_t launch_transport(const TransportArgs &a, int grid, int block, cudaStream_t s);
+cudaError_t launch_debug_sample(const float *tab, const Phys &phys, int kind, float p0, int material,
+                                const float *spec, int n_spec, uint64_t n, uint64_t seed, float *out,
+                                cudaStream_t s);
+
+}  // namespace gm

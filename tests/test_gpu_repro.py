@@ -1,0 +1,118 @@
+"""Scheduling independence: the dose tally is bit-identical whatever the launch
+shape, the history split, the warp-aggregation mode or the overflow path,
+because each particle's random stream depends only on (seed, history,
+lineage, draw) and energies are integers."""
+import numpy as np
+import pytest
+
+import paper_1101_1245_gb300 as g
+import workloads as W
+from tests.gpu_common import make_ctx
+
+pytestmark = pytest.mark.gpu
+
+
+def _plan():
+    ph = W.z_slabs((24, 20, 32), 0.5, [(3.0, W.MAT_WATER, 1.0), (2.0, W.MAT_BONE, 1.85),
+                                        (4.0, W.MAT_LUNG, 0.26), (1e9, W.MAT_WATER, 1.0)])
+    return ph
+
+
+def _dose(ctx, ph, src, n, seed, splits=(None,)):
+    pid = ctx.create_phantom(ph)
+    plan = ctx.plan_open(pid, src, seed, 16)
+    for part in splits:
+        ctx.run([plan], [part if part is not None else n])
+    import torch
+    d = torch.zeros(ph.nvox, dtype=torch.float64, device="cuda")
+    s = torch.zeros(ph.nvox, dtype=torch.float64, device="cuda")
+    st = ctx.plan_result(plan, 0.5, d.data_ptr(), s.data_ptr())
+    ctx.plan_close(plan)
+    ctx.destroy_phantom(pid)
+    return d.cpu().numpy(), s.cpu().numpy(), st
+
+
+SOURCES = {
+    "electron": W.Source(W.ELECTRON, W.BEAM_SQUARE, energy=12.0, center_cm=(6.0, 5.0), field_cm=4.0),
+    "photon": W.Source(W.PHOTON, W.BEAM_SQUARE, energy=15.0, center_cm=(6.0, 5.0), field_cm=4.0),
+}
+
+
+@pytest.fixture(scope="module")
+def reference():
+    ctx = make_ctx()
+    ph = _plan()
+    out = {k: _dose(ctx, ph, src, 40_000, 99) for k, src in SOURCES.items()}
+    ctx.close()
+    return ph, out
+
+
+@pytest.mark.parametrize("kind", ["electron", "photon"])
+@pytest.mark.parametrize("launch", [
+    dict(),
+    dict(block_threads=256, blocks_per_sm=2),
+    dict(block_threads=128, blocks_per_sm=3, chunk=8, refill_low=30, switch_high=64,
+         stack_capacity=128),
+    dict(flags=g.LAUNCH_WARP_AGGREGATE),
+    dict(stack_capacity=128, switch_high=64, overflow_capacity=1 << 16, chunk=256),
+])
+def test_bit_identical_across_launch_shapes(reference, kind, launch):
+    ph, out = reference
+    ctx = make_ctx(**launch)
+    d, s, st = _dose(ctx, ph, SOURCES[kind], 40_000, 99)
+    ctx.close()
+    d0, s0, st0 = out[kind]
+    assert np.array_equal(d, d0)
+    assert np.array_equal(s, s0)
+    for k in ("e_incident", "e_deposited", "e_escaped", "e_rest", "n_electron_steps",
+              "n_photon_events", "n_hard_real"):
+        assert st[k] == st0[k], k
+    assert st["e_deposited"] + st["e_escaped"] + st["e_rest"] == st["e_incident"]
+
+
+@pytest.mark.parametrize("kind", ["electron", "photon"])
+def test_split_runs_equal_one_run(reference, kind):
+    ph, out = reference
+    ctx = make_ctx()
+    d, s, st = _dose(ctx, ph, SOURCES[kind], 40_000, 99, splits=(10_000, 17_000, 13_000))
+    ctx.close()
+    assert np.array_equal(d, out[kind][0])
+    assert np.array_equal(s, out[kind][1])
+
+
+@pytest.mark.parametrize("kind", ["electron", "photon"])
+def test_overflow_path_is_lossless(kind):
+    """Small stacks without high-water switching spill to the global queue;
+    the spilled particles finish in further launches with the same result."""
+    ph = _plan()
+    ctx = make_ctx(stack_capacity=128, switch_high=128, overflow_capacity=1 << 18)
+    a = _dose(ctx, ph, SOURCES[kind], 20_000, 5)
+    ctx.close()
+    ctx = make_ctx()
+    b = _dose(ctx, ph, SOURCES[kind], 20_000, 5)
+    ctx.close()
+    assert a[2]["n_spilled"] > 0 and a[2]["n_launches"] > 1
+    assert np.array_equal(a[0], b[0])
+    assert np.array_equal(a[1], b[1])
+
+
+def test_queue_overflow_is_reported_not_dropped():
+    ph = W.homogeneous((16, 16, 16), 0.5, W.MAT_WATER, 1.0)
+    ctx = make_ctx(stack_capacity=128, switch_high=128, overflow_capacity=64)
+    pid = ctx.create_phantom(ph)
+    plan = ctx.plan_open(pid, W.Source(W.PHOTON, W.BEAM_SQUARE, energy=15.0, center_cm=(4, 4),
+                                       field_cm=4.0), 3, 8)
+    with pytest.raises(g.GpumcdError) as e:
+        ctx.run([plan], [200_000])
+    assert e.value.status == g.ERR_QUEUE_OVERFLOW
+    ctx.plan_close(plan)
+    ctx.destroy_phantom(pid)
+    ctx.close()
+
+
+def test_seed_changes_result(reference):
+    ph, out = reference
+    ctx = make_ctx()
+    d, _, _ = _dose(ctx, ph, SOURCES["photon"], 40_000, 100)
+    ctx.close()
+    assert not np.array_equal(d, out["photon"][0])
