@@ -213,6 +213,33 @@ gpumcd_status gpumcd_plan_histories(gpumcd_ctx *ctx, int32_t plan_id, uint64_t *
 /* Device bytes the context currently holds, and its budget. */
 gpumcd_status gpumcd_memory(gpumcd_ctx *ctx, uint64_t *used_bytes, uint64_t *budget_bytes);
 
+/* ---- allocation-free result ---------------------------------------------- */
+
+/* Largest phantom, in voxels, that gpumcd_plan_result_noalloc accepts. */
+#define GPUMCD_NOALLOC_MAX_VOXELS 67108864
+
+/* The paper has no counterpart to this call.
+ *
+ * Same result as gpumcd_plan_result, but the call allocates no memory at all.
+ * It is meant for callers that cannot allocate device memory when they ask for
+ * a result: a serving loop whose HBM budget is already committed in full to
+ * resident phantoms and tallies, or a latency-bound loop in which a
+ * cudaMalloc/cudaFree pair would stall the device.  dose_out and sigma_out
+ * (device, nx*ny*nz doubles) are required here.
+ *
+ * Its reduction scratch is a fixed array of 128 KiB in the library's device
+ * code, which every GPU that loads the library holds until the process exits.
+ * That array bounds the phantom to GPUMCD_NOALLOC_MAX_VOXELS voxels; a larger
+ * phantom returns GPUMCD_ERR_INVALID_ARG.  The first call on a device looks up
+ * the array's device address, so make that first call before any stream
+ * capture.  Every call reuses the same array: calls whose work overlaps on the
+ * GPU (other streams or other host threads) race, so serialize them.  The call
+ * returns once the fold has finished; a plan with no histories yet returns
+ * GPUMCD_ERR_STATE. */
+gpumcd_status gpumcd_plan_result_noalloc(gpumcd_ctx *ctx, int32_t plan_id, double threshold_frac,
+                                         double *dose_out, double *sigma_out, void *stream,
+                                         gpumcd_run_stats *stats);
+
 /* ---- launch tuning ------------------------------------------------------ */
 gpumcd_status gpumcd_set_launch(gpumcd_ctx *ctx, const gpumcd_launch *launch);
 gpumcd_status gpumcd_get_launch(gpumcd_ctx *ctx, gpumcd_launch *launch);

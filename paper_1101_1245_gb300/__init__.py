@@ -115,6 +115,7 @@ SIGNATURES = {
     "gpumcd_run": (_ST, [_CTX, _I32, C.POINTER(_I32), C.POINTER(_U64), _P]),
     "gpumcd_plan_result": (_ST, [_CTX, _I32, _D, _P, _P, _P, C.POINTER(RunStats)]),
     "gpumcd_plan_histories": (_ST, [_CTX, _I32, C.POINTER(_U64)]),
+    "gpumcd_plan_result_noalloc": (_ST, [_CTX, _I32, _D, _P, _P, _P, C.POINTER(RunStats)]),
     "gpumcd_memory": (_ST, [_CTX, C.POINTER(_U64), C.POINTER(_U64)]),
     "gpumcd_set_launch": (_ST, [_CTX, C.POINTER(Launch)]),
     "gpumcd_get_launch": (_ST, [_CTX, C.POINTER(Launch)]),

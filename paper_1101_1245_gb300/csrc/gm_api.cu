@@ -693,6 +693,47 @@ gpumcd_status gpumcd_plan_result(gpumcd_ctx *c, int32_t plan_id, double thr, dou
     return GPUMCD_OK;
 }
 
+gpumcd_status gpumcd_plan_result_noalloc(gpumcd_ctx *c, int32_t plan_id, double thr, double *dose, double *sigma,
+                                         void *stream, gpumcd_run_stats *stats) {
+    if (!c || !dose || !sigma) return GPUMCD_ERR_INVALID_ARG;
+    auto it = c->plans.find(plan_id);
+    if (it == c->plans.end()) return GPUMCD_ERR_NOT_FOUND;
+    if (!(thr >= 0.0 && thr <= 1.0)) return GPUMCD_ERR_INVALID_ARG;
+    Plan &p = it->second;
+    const Phantom &ph = c->phantoms.at(p.phantom);
+    if (ph.nvox > (uint64_t)GPUMCD_NOALLOC_MAX_VOXELS) return GPUMCD_ERR_INVALID_ARG;
+    const uint64_t N = p.hist_done;
+    if (N == 0) return GPUMCD_ERR_STATE;
+    ST(set_device(c));
+    cudaStream_t s = pick(c, stream);
+    double h_nb[64] = {0};
+    const uint64_t cyc = 32ull * p.W;
+    for (uint32_t b = 0; b < p.W; ++b) {
+        const uint64_t full = N / cyc, rem = N % cyc;
+        uint64_t extra = rem > 32ull * b ? rem - 32ull * b : 0;
+        if (extra > 32) extra = 32;
+        h_nb[b] = (double)(32ull * full + extra);
+    }
+    unsigned long long res[4] = {0, 0, 0, 0}, led[4] = {0, 0, 0, 0};
+    const double inv_vol = 1.0 / (ph.voxel[0] * ph.voxel[1] * ph.voxel[2]);
+    CK(launch_fold_noalloc(c->device, (const unsigned long long *)p.tally.p, (const uint32_t *)ph.vox.p, ph.nvox,
+                           (int)p.W, h_nb, (double)N, inv_vol, thr, dose, sigma, s, res));
+    CK(cudaMemcpyAsync(led, p.ledger.p, sizeof led, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (stats) {
+        *stats = p.acc;
+        stats->histories = N;
+        stats->n_batches = p.W;
+        stats->e_incident = led[0];
+        stats->e_escaped = led[1];
+        stats->e_rest = led[2];
+        stats->e_deposited = res[1];
+        memcpy(&stats->d_max_gy, &res[0], 8);
+        memcpy(&stats->s_thr, &res[2], 8);
+    }
+    return GPUMCD_OK;
+}
+
 static gpumcd_status simulate_impl(gpumcd_ctx *c, int32_t phantom_id, const gpumcd_source *src, uint64_t n,
                                    uint64_t seed, double target, double *dose, double *sigma, bool host,
                                    cudaStream_t s, gpumcd_run_stats *stats) {

@@ -32,6 +32,9 @@ cudaError_t launch_sthr(const double *dose, const double *sigma, uint64_t nvox,
                         unsigned long long *count, int n_sm, cudaStream_t s);
 cudaError_t launch_sum_u64(const unsigned long long *a, uint64_t n, unsigned long long *out, int n_sm,
                            cudaStream_t s);
+cudaError_t launch_fold_noalloc(int device, const unsigned long long *tally, const uint32_t *vox, uint64_t nvox,
+                                int W, const double *n_b, double n_tot, double inv_vol, double thr, double *dose,
+                                double *sigma, cudaStream_t s, unsigned long long result[4]);
 cudaError_t launch_philox(const uint32_t *ctr, uint2 key, uint64_t n, int curand, uint32_t *out,
                           cudaStream_t s);
 

@@ -494,4 +494,228 @@ cudaError_t launch_philox(const uint32_t *ctr, uint2 key, uint64_t n, int curand
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Allocation-free fold (gpumcd_plan_result_noalloc).
+//
+// The same dose / uncertainty fold as k_fold, with its reduction scratch in a
+// file-scope device array instead of device memory allocated at run time.
+// Each block folds one fixed range of voxels and writes its partial results
+// to its own slots of the array; single-block kernels then combine the
+// partials in a fixed order.  Every call rewrites the slots it reads, so
+// nothing needs clearing; calls that overlap on the GPU share the array and
+// race.
+// ---------------------------------------------------------------------------
+namespace noalloc {
+
+constexpr int kThreads = 256;
+constexpr int kVoxPerThread = 64;
+constexpr uint64_t kVoxPerBlock = (uint64_t)kThreads * kVoxPerThread;
+constexpr int kMaxBlocks = GPUMCD_NOALLOC_MAX_VOXELS / (kThreads * kVoxPerThread);
+static_assert((uint64_t)kMaxBlocks * kVoxPerBlock == GPUMCD_NOALLOC_MAX_VOXELS, "exact block count");
+
+// [kMaxBlocks][4] partials (max dose bits, deposited energy, sum sigma/D,
+// count) followed by 4 result words (D_max bits, deposited, s_thr bits, count).
+static __device__ __align__(256) unsigned long long scratch[kMaxBlocks * 4 + 4];
+
+template <int W>
+__global__ void k_fold_blocks(const unsigned long long *tally, const uint32_t *vox, uint64_t nvox,
+                              const __grid_constant__ FoldArgs fa, double n_tot, double inv_vol,
+                              double *dose, double *sigma, unsigned long long *part) {
+    __shared__ double smax[kThreads / 32];
+    __shared__ unsigned long long ssum[kThreads / 32];
+    const uint64_t v0 = blockIdx.x * kVoxPerBlock;
+    double local_max = 0.0;
+    unsigned long long local_sum = 0;
+    for (int k = 0; k < kVoxPerThread; ++k) {
+        const uint64_t v = v0 + (uint64_t)k * kThreads + threadIdx.x;
+        if (v >= nvox) break;
+        unsigned long long s[W];
+        unsigned long long tot = 0;
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            s[b] = __ldcs(tally + (uint64_t)b * nvox + v);
+            tot += s[b];
+        }
+        const double mean = (double)tot / n_tot;
+        double acc = 0.0;
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            const double t = fma(-fa.n_b[b], mean, (double)s[b]);
+            acc = fma(t, t, acc);
+        }
+        const double var = acc * ((double)W / ((double)(W - 1) * n_tot * n_tot));
+        const double rho = (double)(vox[v] >> 4) * (double)kRhoQ;
+        const double scale = kQ * kMeVPerGramToGy * inv_vol / rho;
+        const double dv = mean * scale;
+        dose[v] = dv;
+        sigma[v] = sqrt(var) * scale;
+        local_max = fmax(local_max, dv);
+        local_sum += tot;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        local_max = fmax(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
+        local_sum += __shfl_xor_sync(0xffffffffu, local_sum, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        smax[threadIdx.x >> 5] = local_max;
+        ssum[threadIdx.x >> 5] = local_sum;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        unsigned long long t = 0;
+        for (int i = 0; i < kThreads / 32; ++i) {
+            m = fmax(m, smax[i]);
+            t += ssum[i];
+        }
+        part[4 * blockIdx.x + 0] = (unsigned long long)__double_as_longlong(m);
+        part[4 * blockIdx.x + 1] = t;
+    }
+}
+
+// Combine the per-block maxima and deposits (one block, fixed order).
+__global__ void k_combine_max(unsigned long long *part, int n_blocks) {
+    __shared__ double smax[kThreads];
+    __shared__ unsigned long long ssum[kThreads];
+    double m = 0.0;
+    unsigned long long t = 0;
+    for (int b = threadIdx.x; b < n_blocks; b += kThreads) {
+        m = fmax(m, __longlong_as_double((long long)part[4 * b + 0]));
+        t += part[4 * b + 1];
+    }
+    smax[threadIdx.x] = m;
+    ssum[threadIdx.x] = t;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + w]);
+            ssum[threadIdx.x] += ssum[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[4 * kMaxBlocks + 0] = (unsigned long long)__double_as_longlong(smax[0]);
+        part[4 * kMaxBlocks + 1] = ssum[0];
+    }
+}
+
+// Per-block sums of sigma/D over voxels above thr * D_max.
+__global__ void k_sthr_blocks(const double *dose, const double *sigma, uint64_t nvox, double thr,
+                              unsigned long long *part) {
+    __shared__ double ss[kThreads / 32];
+    __shared__ unsigned long long sc[kThreads / 32];
+    const double cut = thr * __longlong_as_double((long long)part[4 * kMaxBlocks + 0]);
+    const uint64_t v0 = blockIdx.x * kVoxPerBlock;
+    double s = 0.0;
+    unsigned long long c = 0;
+    for (int k = 0; k < kVoxPerThread; ++k) {
+        const uint64_t v = v0 + (uint64_t)k * kThreads + threadIdx.x;
+        if (v >= nvox) break;
+        const double d = dose[v];
+        if (d > cut && d > 0.0) {
+            s += sigma[v] / d;
+            ++c;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        ss[threadIdx.x >> 5] = s;
+        sc[threadIdx.x >> 5] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        unsigned long long b = 0;
+        for (int i = 0; i < kThreads / 32; ++i) {
+            a += ss[i];
+            b += sc[i];
+        }
+        part[4 * blockIdx.x + 2] = (unsigned long long)__double_as_longlong(a);
+        part[4 * blockIdx.x + 3] = b;
+    }
+}
+
+__global__ void k_combine_sthr(unsigned long long *part, int n_blocks) {
+    __shared__ double ss[kThreads];
+    __shared__ unsigned long long sc[kThreads];
+    double s = 0.0;
+    unsigned long long c = 0;
+    for (int b = threadIdx.x; b < n_blocks; b += kThreads) {
+        s += __longlong_as_double((long long)part[4 * b + 2]);
+        c += part[4 * b + 3];
+    }
+    ss[threadIdx.x] = s;
+    sc[threadIdx.x] = c;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            ss[threadIdx.x] += ss[threadIdx.x + w];
+            sc[threadIdx.x] += sc[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double sthr = sc[0] ? ss[0] / (double)sc[0] : 0.0;
+        part[4 * kMaxBlocks + 2] = (unsigned long long)__double_as_longlong(sthr);
+        part[4 * kMaxBlocks + 3] = sc[0];
+    }
+}
+
+}  // namespace noalloc
+
+// The address of the scratch array on `device`, looked up once per device
+// with that device current.  In host code the array's name is only a host-side
+// stand-in, so kernels must be given this address instead.
+static unsigned long long *noalloc_scratch(int device, cudaError_t *err) {
+    static unsigned long long *addr[64] = {nullptr};
+    static bool done[64] = {false};
+    if (device < 0 || device >= 64) {
+        *err = cudaErrorInvalidDevice;
+        return nullptr;
+    }
+    if (!done[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, noalloc::scratch);
+        if (e != cudaSuccess) {
+            *err = e;
+            return nullptr;
+        }
+        addr[device] = (unsigned long long *)p;
+        done[device] = true;
+    }
+    *err = cudaSuccess;
+    return addr[device];
+}
+
+cudaError_t launch_fold_noalloc(int device, const unsigned long long *tally, const uint32_t *vox, uint64_t nvox,
+                                int W, const double *n_b, double n_tot, double inv_vol, double thr, double *dose,
+                                double *sigma, cudaStream_t s, unsigned long long result[4]) {
+    cudaError_t e;
+    unsigned long long *part = noalloc_scratch(device, &e);
+    if (!part) return e;
+    FoldArgs fa;
+    for (int b = 0; b < 64; ++b) fa.n_b[b] = b < W ? n_b[b] : 0.0;
+    const int nb = (int)((nvox + noalloc::kVoxPerBlock - 1) / noalloc::kVoxPerBlock);
+    using namespace noalloc;
+    switch (W) {
+        case 8: k_fold_blocks<8><<<nb, kThreads, 0, s>>>(tally, vox, nvox, fa, n_tot, inv_vol, dose, sigma, part); break;
+        case 16: k_fold_blocks<16><<<nb, kThreads, 0, s>>>(tally, vox, nvox, fa, n_tot, inv_vol, dose, sigma, part); break;
+        case 32: k_fold_blocks<32><<<nb, kThreads, 0, s>>>(tally, vox, nvox, fa, n_tot, inv_vol, dose, sigma, part); break;
+        case 64: k_fold_blocks<64><<<nb, kThreads, 0, s>>>(tally, vox, nvox, fa, n_tot, inv_vol, dose, sigma, part); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_combine_max<<<1, kThreads, 0, s>>>(part, nb);
+    k_sthr_blocks<<<nb, kThreads, 0, s>>>(dose, sigma, nvox, thr, part);
+    k_combine_sthr<<<1, kThreads, 0, s>>>(part, nb);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = cudaMemcpyAsync(result, part + 4 * kMaxBlocks, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
 }  // namespace gm
