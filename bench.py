@@ -30,20 +30,17 @@ METRIC = "histories/s (1e6 e- + 4e6 photons, 15 MeV, 128^3 water, to FP64 dose +
 UNIT = "histories/s"
 N_E, N_G = 1_000_000, 4_000_000
 
-# Warp-instructions of useful work per unit, from ncu (smsp__thread_inst_executed.sum / 32
-# divided by the kernel's own event counts) on the same workload: per electron
-# condensed-history step and per photon Woodcock event.  See profiles/.
-INST_PER_E_STEP = None
-INST_PER_PH_EVENT = None
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="run each beam once at 1/5 of its histories (small case for ncu) and exit")
     return ap.parse_args()
 
 
@@ -53,7 +50,7 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -68,7 +65,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -248,12 +245,13 @@ def run_ours(args):
     st_e, st_g = stats[-1]
     launches = st_e["n_launches"] + st_g["n_launches"] + 2 * 3  # transport + fold, s_thr, ledger sum
     clocks = clk.summary()
-    steps_e = st_e["n_electron_steps"] + st_g["n_electron_steps"]
-    events_g = st_e["n_photon_events"] + st_g["n_photon_events"]
+    ev_e = st_e["n_electron_steps"] + st_e["n_photon_events"]
+    ev_g = st_g["n_electron_steps"] + st_g["n_photon_events"]
     kern_ms = st_e["transport_ms"] + st_g["transport_ms"]
     import paper_1101_1245_gb300.roofline as rl
-    roof = rl.alu_roofline(steps_e, events_g, kern_ms, clocks.get("sm_mhz"),
-                           torch.cuda.get_device_properties(dev).multi_processor_count)
+    roof = rl.alu_roofline(ev_e, ev_g, kern_ms, clocks.get("sm_mhz"),
+                           torch.cuda.get_device_properties(dev).multi_processor_count,
+                           launches=st_e["n_launches"] + st_g["n_launches"])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -280,8 +278,32 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_ncu_case():
+    """Each beam of the step once at 1/5 of its histories, untimed: the small
+    case profiled with ncu --set full (one launch of the transport kernel per beam)."""
+    import paper_1101_1245_gb300 as g
+    import workloads as W
+
+    ctx = g.engine(0)
+    for part, n in ((W.ELECTRON, N_E // 5), (W.PHOTON, N_G // 5)):
+        pl = W.config2(part)
+        pid = ctx.create_phantom(pl.phantom)
+        plan = ctx.plan_open(pid, pl.source, 5, 32)
+        ctx.run([plan], [n])
+        st = ctx.plan_result(plan, 0.5)
+        print(json.dumps({"case": pl.name, "histories": n, **{k: st[k] for k in (
+            "n_electron_steps", "n_photon_events", "n_hard_real", "n_launches", "transport_ms")}}),
+            flush=True)
+        ctx.plan_close(plan)
+        ctx.destroy_phantom(pid)
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.ncu_case:
+        run_ncu_case()
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -227,11 +227,11 @@ gpumcd_status gpumcd_init(gpumcd_ctx **out, int32_t device, uint64_t hbm_budget_
         return cuda_status(e);
     }
     c->launch.block_threads = 512;
-    c->launch.blocks_per_sm = 1;
-    c->launch.stack_capacity = 256;
-    c->launch.switch_high = 128;
+    c->launch.blocks_per_sm = 2;
+    c->launch.stack_capacity = 512;
+    c->launch.switch_high = 200;
     c->launch.refill_low = 16;
-    c->launch.chunk = 64;
+    c->launch.chunk = 32;
     c->launch.overflow_capacity = 1u << 20;
     c->launch.flags = 0;
     *out = c;
@@ -585,7 +585,7 @@ gpumcd_status gpumcd_run(gpumcd_ctx *c, int32_t n_plans, const int32_t *ids, con
             A.in_count[t] = in_count[t];
         }
         CK(cudaMemsetAsync(dc->qcur[bo], 0, sizeof(dc->qcur[bo]), s));
-        CK(launch_transport(A, grid, block, s));
+        CK(launch_transport(A, grid, block, (int)c->launch.blocks_per_sm, s));
         ++launches;
         CK(cudaMemcpyAsync(c->h_control, dc, sizeof(Control), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -805,7 +805,12 @@ gpumcd_status gpumcd_set_launch(gpumcd_ctx *c, const gpumcd_launch *l) {
     if (l->overflow_capacity) n.overflow_capacity = l->overflow_capacity;
     n.flags = l->flags;
     if (n.block_threads % 32 || n.block_threads < 32 || n.block_threads > 512) return GPUMCD_ERR_INVALID_ARG;
-    if (n.blocks_per_sm < 1 || n.blocks_per_sm > 3) return GPUMCD_ERR_INVALID_ARG;
+    if (n.blocks_per_sm < 1 || n.blocks_per_sm > 4) return GPUMCD_ERR_INVALID_ARG;
+    // supported (threads, CTAs/SM) pairs follow the kernel's launch-bound variants
+    const bool ok = (n.blocks_per_sm == 1 && n.block_threads <= 512) ||
+                    (n.blocks_per_sm == 2 && n.block_threads <= 512) ||
+                    (n.blocks_per_sm >= 3 && n.block_threads <= 256);
+    if (!ok) return GPUMCD_ERR_INVALID_ARG;
     if (n.stack_capacity < 128 || n.stack_capacity > (1u << 16)) return GPUMCD_ERR_INVALID_ARG;
     if (n.switch_high < 32 || n.switch_high > n.stack_capacity) return GPUMCD_ERR_INVALID_ARG;
     if (n.refill_low > 32 || n.chunk < 1 || n.chunk > 4096) return GPUMCD_ERR_INVALID_ARG;

@@ -100,10 +100,15 @@ __device__ __forceinline__ uint32_t voxel_index(const PlanDev &P, float x, float
     return (uint32_t)ix + (uint32_t)P.nx * ((uint32_t)iy + (uint32_t)P.ny * (uint32_t)iz);
 }
 
+// Fire-and-forget 64-bit add into the tally (no value comes back).
+__device__ __forceinline__ void red_add_u64(unsigned long long *addr, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(addr), "l"(v) : "memory");
+}
+
 __device__ __forceinline__ void deposit(const PlanDev &P, uint32_t hist, uint32_t idx, uint32_t e) {
     if (e == 0u) return;
     const uint32_t b = (hist >> 5) & P.bmask;
-    atomicAdd(P.tally + (size_t)b * P.nvox + idx, (unsigned long long)e);
+    red_add_u64(P.tally + (size_t)b * P.nvox + idx, (unsigned long long)e);
 }
 
 // Deposit at a convergent point (all 32 lanes call it): lanes that hit the
@@ -120,7 +125,7 @@ __device__ __forceinline__ void deposit_aggregated(const PlanDev &P, uint32_t hi
     const unsigned lo = __reduce_add_sync(peers, e & 0xFFFFu);
     const unsigned hi = __reduce_add_sync(peers, e >> 16);
     if ((threadIdx.x & 31) == __ffs(peers) - 1)
-        atomicAdd(addr, ((unsigned long long)hi << 16) + (unsigned long long)lo);
+        red_add_u64(addr, ((unsigned long long)hi << 16) + (unsigned long long)lo);
 }
 
 __device__ __forceinline__ void ledger_add(const Smem &S, uint32_t plan, int which, uint32_t e) {
@@ -756,7 +761,8 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__global__ void __launch_bounds__(512, 1) k_transport(const __grid_constant__ TransportArgs A) {
+template <int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant__ TransportArgs A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *tab = (float *)smem_raw;
     PlanDev *plans = (PlanDev *)(smem_raw + TAB_BYTES);
@@ -889,13 +895,37 @@ size_t transport_smem_bytes(int /*block_threads*/) {
            sizeof(unsigned long long) * (CNT_N + 3 * GPUMCD_MAX_PLANS_PER_RUN + 1) + sizeof(CtaFlags);
 }
 
-cudaError_t transport_configure(int block_threads) {
-    return cudaFuncSetAttribute(k_transport, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)transport_smem_bytes(block_threads));
+// Instantiations by launch bound (threads per CTA, CTAs per SM): the bound
+// sets the register budget, so the resident-CTA count is a launch choice.
+typedef void (*TransportKernel)(const TransportArgs);
+struct Variant {
+    int max_threads, min_blocks;
+    TransportKernel fn;
+};
+static const Variant kVariants[] = {
+    {512, 1, k_transport<512, 1>}, {384, 2, k_transport<384, 2>}, {512, 2, k_transport<512, 2>},
+    {256, 3, k_transport<256, 3>}, {256, 4, k_transport<256, 4>},
+};
+
+static TransportKernel pick_variant(int block, int blocks_per_sm) {
+    for (const Variant &v : kVariants)
+        if (block <= v.max_threads && blocks_per_sm <= v.min_blocks) return v.fn;
+    return nullptr;
 }
 
-cudaError_t launch_transport(const TransportArgs &a, int grid, int block, cudaStream_t s) {
-    k_transport<<<grid, block, transport_smem_bytes(block), s>>>(a);
+cudaError_t transport_configure(int block_threads) {
+    for (const Variant &v : kVariants) {
+        cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)transport_smem_bytes(block_threads));
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_transport(const TransportArgs &a, int grid, int block, int blocks_per_sm, cudaStream_t s) {
+    TransportKernel fn = pick_variant(block, blocks_per_sm);
+    if (!fn) return cudaErrorInvalidConfiguration;
+    fn<<<grid, block, transport_smem_bytes(block), s>>>(a);
     return cudaGetLastError();
 }
 

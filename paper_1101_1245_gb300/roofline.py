@@ -6,23 +6,28 @@ ceiling is 4 warp-instructions per clock per SM (one per SM sub-partition),
 times the SM count and the SM clock sampled during the timed region.
 
 The algorithmic work of one launch is counted in warp-instructions that a
-fully converged warp would issue: the per-unit costs below (from ncu,
-smsp__thread_inst_executed.sum / 32 per electron step and per photon event on
-the 15 MeV 128^3 water workload) times the step and event counts that the
-kernel itself reports.
+fully converged warp would issue: the per-unit costs below times the transport
+events (electron condensed-history steps plus photon Woodcock events) that the
+kernel itself counts.  The per-unit costs come from ncu on the same workload
+at reduced history counts (smsp__inst_executed.sum x
+smsp__thread_inst_executed_per_inst_executed.ratio / 32, divided by the
+kernel's event counts), separately for the electron and the photon beam
+because their mixes of step and event types differ.
 """
 from __future__ import annotations
 
 from typing import Optional
 
-# warp-instructions per electron condensed-history step / per photon Woodcock event
-INST_PER_E_STEP: Optional[float] = None
-INST_PER_PH_EVENT: Optional[float] = None
-# DRAM bytes (read + write) per transport launch of the benchmark step, from ncu
-TRAFFIC_BYTES_PER_LAUNCH: Optional[float] = None
+# converged warp-instructions per transport event, electron beam / photon beam
+INST_PER_EVENT_E_BEAM: Optional[float] = 19.68
+INST_PER_EVENT_PH_BEAM: Optional[float] = 18.81
+# DRAM bytes (read + write) per transport launch of the benchmark step, from ncu on
+# the same workload at 1/5 of its histories, scaled by histories (733 MB electron
+# launch, 3.47 GB photon launch); None once the kernel has changed since the capture
+TRAFFIC_BYTES_PER_LAUNCH: Optional[float] = 2.10e9
 
 
-def alu_roofline(e_steps: int, ph_events: int, kernel_ms: float, sm_mhz: Optional[float],
+def alu_roofline(events_e_beam: int, events_ph_beam: int, kernel_ms: float, sm_mhz: Optional[float],
                  n_sm: int, launches: int = 2) -> dict:
     peak = None
     if sm_mhz:
@@ -30,8 +35,8 @@ def alu_roofline(e_steps: int, ph_events: int, kernel_ms: float, sm_mhz: Optiona
     out = {"bound": "alu", "unit": "Gwarp-inst/s", "peak": peak, "achieved": None, "frac": None,
            "traffic": TRAFFIC_BYTES_PER_LAUNCH,
            "peak_basis": f"{n_sm} SMs x 4 warp-inst/clk x median sampled SM clock"}
-    if INST_PER_E_STEP is not None and INST_PER_PH_EVENT is not None and kernel_ms > 0:
-        work = e_steps * INST_PER_E_STEP + ph_events * INST_PER_PH_EVENT
+    if INST_PER_EVENT_E_BEAM is not None and INST_PER_EVENT_PH_BEAM is not None and kernel_ms > 0:
+        work = events_e_beam * INST_PER_EVENT_E_BEAM + events_ph_beam * INST_PER_EVENT_PH_BEAM
         out["achieved"] = work / (kernel_ms / 1e3) / 1e9
         out["work_warp_inst_per_launch"] = work / max(launches, 1)
         if peak:

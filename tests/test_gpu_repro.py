@@ -80,28 +80,33 @@ def test_split_runs_equal_one_run(reference, kind):
     assert np.array_equal(s, out[kind][1])
 
 
+# A small grid (2 warps per SM) and no high-water switching: each warp's
+# stacks fill past their headroom and spill to the global overflow queue.
+SPILL = dict(block_threads=64, blocks_per_sm=1, stack_capacity=128, switch_high=128)
+
+
 @pytest.mark.parametrize("kind", ["electron", "photon"])
 def test_overflow_path_is_lossless(kind):
-    """Small stacks without high-water switching spill to the global queue;
-    the spilled particles finish in further launches with the same result."""
+    """Spilled particles finish in further launches with the same result."""
     ph = _plan()
-    ctx = make_ctx(stack_capacity=128, switch_high=128, overflow_capacity=1 << 18)
-    a = _dose(ctx, ph, SOURCES[kind], 20_000, 5)
+    n = 200_000 if kind == "photon" else 40_000
+    ctx = make_ctx(overflow_capacity=1 << 20, **SPILL)
+    a = _dose(ctx, ph, SOURCES[kind], n, 5)
     ctx.close()
     ctx = make_ctx()
-    b = _dose(ctx, ph, SOURCES[kind], 20_000, 5)
+    b = _dose(ctx, ph, SOURCES[kind], n, 5)
     ctx.close()
-    assert a[2]["n_spilled"] > 0 and a[2]["n_launches"] > 1
+    assert a[2]["n_spilled"] > 0 and a[2]["n_launches"] > 1, a[2]
+    assert b[2]["n_spilled"] == 0 and b[2]["n_launches"] == 1
     assert np.array_equal(a[0], b[0])
     assert np.array_equal(a[1], b[1])
 
 
 def test_queue_overflow_is_reported_not_dropped():
-    ph = W.homogeneous((16, 16, 16), 0.5, W.MAT_WATER, 1.0)
-    ctx = make_ctx(stack_capacity=128, switch_high=128, overflow_capacity=64)
+    ph = _plan()
+    ctx = make_ctx(overflow_capacity=64, **SPILL)
     pid = ctx.create_phantom(ph)
-    plan = ctx.plan_open(pid, W.Source(W.PHOTON, W.BEAM_SQUARE, energy=15.0, center_cm=(4, 4),
-                                       field_cm=4.0), 3, 8)
+    plan = ctx.plan_open(pid, SOURCES["photon"], 5, 8)
     with pytest.raises(g.GpumcdError) as e:
         ctx.run([plan], [200_000])
     assert e.value.status == g.ERR_QUEUE_OVERFLOW
