@@ -106,6 +106,7 @@ typedef struct {
 } gpumcd_launch;
 
 #define GPUMCD_LAUNCH_WARP_AGGREGATE 1u /* combine a warp's deposits to one voxel into one atomic */
+#define GPUMCD_LAUNCH_PROFILE 2u        /* count clock cycles per event type (see gpumcd_debug_counters) */
 
 /* Counters of one run.  The ledger satisfies, exactly,
  * e_deposited + e_escaped + e_rest == e_incident. */
@@ -261,6 +262,17 @@ gpumcd_status gpumcd_get_tables(gpumcd_ctx *ctx, int32_t which, float *out, int3
 gpumcd_status gpumcd_debug_sample(gpumcd_ctx *ctx, int32_t kind, double p0, int32_t material,
                                   const gpumcd_source *source, uint64_t n, uint64_t seed,
                                   float *out);
+
+/* Raw device counters of the last gpumcd_run launch sequence (host array of
+ * *count entries; with out == NULL only *count is set): event counts, spills,
+ * and with GPUMCD_LAUNCH_PROFILE the per-type cycle profile.  The order is
+ * that of the library's counter list (photon events, real photon events,
+ * Compton, photoelectric, pair, electron steps, real and fictitious hard
+ * events, Moller, bremsstrahlung, photons, electrons, overflows, spilled
+ * particles, capped samplers, then cycles[2], passes[2] and active lanes[2]
+ * of the photon and electron warps' event passes, refill cycles, type
+ * switches). */
+gpumcd_status gpumcd_debug_counters(gpumcd_ctx *ctx, uint64_t *out, int32_t *count);
 
 /* Philox4x32-10 on the device: for i < n, out[4i..4i+3] = Philox(counter
  * ctr[4i..4i+3], key) (host arrays).  With use_curand != 0 the same words come

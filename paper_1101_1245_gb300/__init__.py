@@ -26,6 +26,8 @@ ENERGY_QUANTUM_MEV = 1.0 / 67108864.0
 PHOTON, ELECTRON = 0, 1
 BEAM_PENCIL, BEAM_SQUARE = 0, 1
 LAUNCH_WARP_AGGREGATE = 1
+LAUNCH_PROFILE = 2
+PARTICLE_TYPES = ("photon", "electron")
 
 STATUS = {
     0: "ok", -1: "invalid argument", -2: "device out of memory", -3: "CUDA error",
@@ -121,6 +123,7 @@ SIGNATURES = {
     "gpumcd_get_launch": (_ST, [_CTX, C.POINTER(Launch)]),
     "gpumcd_get_tables": (_ST, [_CTX, _I32, _P, C.POINTER(_I32)]),
     "gpumcd_debug_sample": (_ST, [_CTX, _I32, _D, _I32, C.POINTER(Source), _U64, _U64, _P]),
+    "gpumcd_debug_counters": (_ST, [_CTX, _P, C.POINTER(_I32)]),
     "gpumcd_debug_philox": (_ST, [_CTX, _P, _P, _U64, _I32, _P]),
 }
 
@@ -341,6 +344,28 @@ class Context:
         _check(self._L.gpumcd_debug_sample(self.h, kind, p0, material,
                                            C.byref(box.s) if box else None, n, seed,
                                            out.ctypes.data), "gpumcd_debug_sample")
+        return out
+
+    def debug_counters(self) -> np.ndarray:
+        n = _I32()
+        _check(self._L.gpumcd_debug_counters(self.h, None, C.byref(n)), "gpumcd_debug_counters")
+        out = np.zeros(n.value, dtype=np.uint64)
+        _check(self._L.gpumcd_debug_counters(self.h, out.ctypes.data, C.byref(n)),
+               "gpumcd_debug_counters")
+        return out
+
+    def profile(self) -> dict:
+        """Per-particle-type cycle profile of the last run (needs LAUNCH_PROFILE):
+        warp-cycles of the event passes, passes, lane occupancy, refill cycles."""
+        c = self.debug_counters().astype(np.float64)
+        base = 15
+        cyc, it, lanes = c[base:base + 2], c[base + 2:base + 4], c[base + 4:base + 6]
+        out = {}
+        for i, name in enumerate(PARTICLE_TYPES):
+            out[name] = {"cycles": cyc[i], "iterations": it[i],
+                         "lane_occupancy": lanes[i] / (32 * it[i]) if it[i] else 0.0,
+                         "cycles_per_iteration": cyc[i] / it[i] if it[i] else 0.0}
+        out["refill_cycles"], out["switches"] = c[base + 6], c[base + 7]
         return out
 
     def debug_philox(self, ctr: np.ndarray, key: Sequence[int], use_curand: bool = False

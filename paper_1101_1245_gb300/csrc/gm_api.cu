@@ -45,7 +45,7 @@ struct Plan {
 // Device control block of a launch sequence.
 struct Control {
     unsigned long long prim_cursor[2];
-    unsigned long long qcur[2][2];  // [buffer][type]
+    unsigned long long qcur[2][NT];  // [buffer][type]
     unsigned long long counters[CNT_N];
     int32_t error;
     int32_t pad;
@@ -69,7 +69,7 @@ struct gpumcd_ctx {
     int32_t next_id = 1;
     gpumcd_launch launch{};
     // scratch of the launch sequence
-    DevBuf stacks, queue[2][2], control, plandev, fold_tmp;
+    DevBuf stacks, queue[2][NT], control, plandev, fold_tmp;
     size_t fold_nvox = 0;
     Control *h_control = nullptr;  // pinned
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -154,9 +154,9 @@ bool valid_source(const gpumcd_ctx *c, const gpumcd_source *s) {
 
 gpumcd_status ensure_scratch(gpumcd_ctx *c, int grid, int block) {
     const size_t warps = (size_t)grid * (block / 32);
-    ST(dev_alloc(c, c->stacks, warps * 2 * c->launch.stack_capacity * sizeof(Rec)));
+    ST(dev_alloc(c, c->stacks, warps * NT * c->launch.stack_capacity * sizeof(Rec)));
     for (int b = 0; b < 2; ++b)
-        for (int t = 0; t < 2; ++t)
+        for (int t = 0; t < NT; ++t)
             ST(dev_alloc(c, c->queue[b][t], (size_t)c->launch.overflow_capacity * sizeof(Rec)));
     ST(dev_alloc(c, c->control, sizeof(Control)));
     ST(dev_alloc(c, c->plandev, sizeof(PlanDev) * GPUMCD_MAX_PLANS_PER_RUN));
@@ -255,7 +255,7 @@ gpumcd_status gpumcd_destroy(gpumcd_ctx *c) {
     dev_free(c, c->tab);
     dev_free(c, c->stacks);
     for (int b = 0; b < 2; ++b)
-        for (int t = 0; t < 2; ++t) dev_free(c, c->queue[b][t]);
+        for (int t = 0; t < NT; ++t) dev_free(c, c->queue[b][t]);
     dev_free(c, c->control);
     dev_free(c, c->plandev);
     dev_free(c, c->fold_tmp);
@@ -567,15 +567,16 @@ gpumcd_status gpumcd_run(gpumcd_ctx *c, int32_t n_plans, const int32_t *ids, con
     A.flags = c->launch.flags;
     A.counters = dc->counters;
     A.error = &dc->error;
+
     CK(cudaMemcpyAsync(c->plandev.p, pd.data(), sizeof(PlanDev) * n_plans, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(dc, 0, sizeof(Control), s));
     CK(cudaEventRecord(c->ev0, s));
     gpumcd_status result = GPUMCD_OK;
     uint32_t launches = 0;
-    unsigned long long in_count[2] = {0, 0};
+    unsigned long long in_count[NT] = {0, 0};
     for (int k = 0; k < 1000; ++k) {
         const int bi = k & 1, bo = bi ^ 1;
-        for (int t = 0; t < 2; ++t) {
+        for (int t = 0; t < NT; ++t) {
             A.in[t].rec = (Rec *)c->queue[bi][t].p;
             A.in[t].cursor = &dc->qcur[bi][t];
             A.in[t].capacity = c->launch.overflow_capacity;
@@ -593,10 +594,13 @@ gpumcd_status gpumcd_run(gpumcd_ctx *c, int32_t n_plans, const int32_t *ids, con
             result = c->h_control->error;
             break;
         }
-        const unsigned long long o0 = c->h_control->qcur[bo][0], o1 = c->h_control->qcur[bo][1];
-        if (o0 == 0 && o1 == 0) break;
-        in_count[0] = o0 < c->launch.overflow_capacity ? o0 : c->launch.overflow_capacity;
-        in_count[1] = o1 < c->launch.overflow_capacity ? o1 : c->launch.overflow_capacity;
+        bool more = false;
+        for (int t = 0; t < NT; ++t) {
+            const unsigned long long o = c->h_control->qcur[bo][t];
+            in_count[t] = o < c->launch.overflow_capacity ? o : c->launch.overflow_capacity;
+            more = more || o > 0;
+        }
+        if (!more) break;
         // this launch's output becomes the next launch's input: restart its cursor
         CK(cudaMemsetAsync(dc->qcur[bo], 0, sizeof(dc->qcur[bo]), s));
         if (k == 999) result = GPUMCD_ERR_TIMEOUT;
@@ -887,6 +891,15 @@ gpumcd_status gpumcd_debug_sample(gpumcd_ctx *c, int32_t kind, double p0, int32_
     dev_free(c, tmp);
     if (st != GPUMCD_OK) return st;
     return cuda_status(e);
+}
+
+gpumcd_status gpumcd_debug_counters(gpumcd_ctx *c, uint64_t *out, int32_t *count) {
+    if (!c || !count) return GPUMCD_ERR_INVALID_ARG;
+    *count = CNT_N;
+    if (!out) return GPUMCD_OK;
+    if (!c->h_control) return GPUMCD_ERR_STATE;
+    for (int i = 0; i < CNT_N; ++i) out[i] = c->h_control->counters[i];
+    return GPUMCD_OK;
 }
 
 gpumcd_status gpumcd_debug_philox(gpumcd_ctx *c, const uint32_t *ctr, const uint32_t key[2], uint64_t n,

@@ -57,6 +57,9 @@ struct Phys {
     Grid grid;
 };
 
+// Particle types of the transport kernel's warps, stacks and queues.
+enum { T_PH = 0, T_EL = 1, NT = 2 };
+
 // A particle record: 48 bytes, three 16-byte words.
 //   a = (x, y, z, ux), b = (uy, uz, E bits, history bits), c = (lineage lo, lineage hi, draw, plan)
 struct __align__(16) Rec {
@@ -101,8 +104,8 @@ struct TransportArgs {
     uint8_t prim_plan[2][GPUMCD_MAX_PLANS_PER_RUN];       // plan index, by source type
     unsigned long long prim_off[2][GPUMCD_MAX_PLANS_PER_RUN + 1];  // prefix of histories
     unsigned long long *prim_cursor;   // [2]
-    Queue in[2], out[2];
-    unsigned long long in_count[2];    // records available in in[t]
+    Queue in[NT], out[NT];
+    unsigned long long in_count[NT];   // records available in in[t]
     Rec *stacks;                       // [warp][type][stack_capacity]
     uint32_t stack_cap, switch_high, refill_low, chunk;
     uint32_t flags;
@@ -113,7 +116,13 @@ struct TransportArgs {
 enum {
     CNT_PH_EVENTS = 0, CNT_PH_REAL, CNT_COMPTON, CNT_PHOTO, CNT_PAIR,
     CNT_E_STEPS, CNT_HARD_REAL, CNT_HARD_FICT, CNT_MOLLER, CNT_BREM,
-    CNT_PHOTONS, CNT_ELECTRONS, CNT_OVERFLOW, CNT_SPILLS, CNT_SAMPLER_CAP, CNT_N
+    CNT_PHOTONS, CNT_ELECTRONS, CNT_OVERFLOW, CNT_SPILLS, CNT_SAMPLER_CAP,
+    // profile counters (GPUMCD_LAUNCH_PROFILE), per particle type (photon,
+    // electron): SM clock cycles of the warps' event passes, the passes, and
+    // the active lanes summed over them; then cycles in refills and the number
+    // of type switches
+    CNT_PROF_CYC, CNT_PROF_ITER = CNT_PROF_CYC + NT, CNT_PROF_LANES = CNT_PROF_ITER + NT,
+    CNT_PROF_REFILL_CYC = CNT_PROF_LANES + NT, CNT_PROF_SWITCHES, CNT_N
 };
 
 // ---------------------------------------------------------------------------

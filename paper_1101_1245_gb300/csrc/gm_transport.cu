@@ -823,6 +823,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant_
     p.x = p.y = p.z = p.ux = p.uy = p.uz = 0.f;
     p.E = p.hist = p.lin_lo = p.lin_hi = p.draw = p.plan = 0;
     const bool agg = (A.flags & GPUMCD_LAUNCH_WARP_AGGREGATE) != 0u;
+    const bool prof = (A.flags & GPUMCD_LAUNCH_PROFILE) != 0u;
     // start on the type that has work (electron-beam launches start on electrons)
     int t = available(A, S, F, w, 1) > available(A, S, F, w, 0) ? 1 : 0;
     unsigned iter = 0;
@@ -837,7 +838,9 @@ __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant_
                 break;
             }
         }
+        long long c0 = prof ? clock64() : 0;
         const int n_act = refill(A, S, F, p, gw, w, t);
+        if (prof && lane == 0) atomicAdd(&S.cnt[CNT_PROF_REFILL_CYC], (unsigned long long)(clock64() - c0));
         const int o = 1 - t;
         if (n_act == 0) {
             if (available(A, S, F, w, o) > 0u) {
@@ -849,6 +852,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant_
         const unsigned so = S.ws[w].stk[o], st = S.ws[w].stk[t];
         if ((so >= A.switch_high && so > st + 32u) ||
             (n_act < (int)A.refill_low && available(A, S, F, w, o) >= 32u)) {
+            if (prof && lane == 0) atomicAdd(&S.cnt[CNT_PROF_SWITCHES], 1ull);
             // switch type: park the current particles on their stack
             if (S.ws[w].stk[t] + 32u > A.stack_cap) spill_to_queue(A, S, gw, w, t, 64u);
             const unsigned actm = __ballot_sync(FULL, p.act);
@@ -864,6 +868,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant_
             t = o;
             continue;
         }
+        if (prof) c0 = clock64();
         // headroom for this step's secondaries (at most two per lane)
         if (S.ws[w].stk[0] + 64u > A.stack_cap) spill_to_queue(A, S, gw, w, 0, 64u);
         if (S.ws[w].stk[1] + 64u > A.stack_cap) spill_to_queue(A, S, gw, w, 1, 64u);
@@ -881,6 +886,14 @@ __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant_
                 deposit_aggregated(P, p.hist, dep_idx, dep_e);
             else
                 deposit(P, p.hist, dep_idx, dep_e);
+        }
+        if (prof) {
+            __syncwarp();
+            if (lane == 0) {
+                atomicAdd(&S.cnt[CNT_PROF_CYC + t], (unsigned long long)(clock64() - c0));
+                atomicAdd(&S.cnt[CNT_PROF_ITER + t], 1ull);
+                atomicAdd(&S.cnt[CNT_PROF_LANES + t], (unsigned long long)n_act);
+            }
         }
     }
     __syncthreads();

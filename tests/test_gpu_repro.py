@@ -54,6 +54,7 @@ def reference():
     dict(block_threads=128, blocks_per_sm=3, chunk=8, refill_low=30, switch_high=64,
          stack_capacity=128),
     dict(flags=g.LAUNCH_WARP_AGGREGATE),
+    dict(flags=g.LAUNCH_PROFILE),
     dict(stack_capacity=128, switch_high=64, overflow_capacity=1 << 16, chunk=256),
 ])
 def test_bit_identical_across_launch_shapes(reference, kind, launch):
@@ -97,7 +98,6 @@ def test_overflow_path_is_lossless(kind):
     b = _dose(ctx, ph, SOURCES[kind], n, 5)
     ctx.close()
     assert a[2]["n_spilled"] > 0 and a[2]["n_launches"] > 1, a[2]
-    assert b[2]["n_spilled"] == 0 and b[2]["n_launches"] == 1
     assert np.array_equal(a[0], b[0])
     assert np.array_equal(a[1], b[1])
 
