@@ -41,6 +41,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run each beam once at 1/5 of its histories (small case for ncu) and exit")
+    ap.add_argument("--workload", default="c2", choices=["c2", "batched", "served"],
+                    help="c2: the contract line; batched: 64 uneven plans in one launch vs alone; "
+                         "served: a Poisson request stream with continuous batching")
+    ap.add_argument("--requests", type=int, default=200, help="served: number of requests")
+    ap.add_argument("--target", type=float, default=0.01, help="served: relative uncertainty target")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="served: HBM budget")
     return ap.parse_args()
 
 
@@ -133,6 +139,21 @@ def oracle_sample(seconds: float = 12.0, seed0: int = 100):
     return done / dt, cores, desc
 
 
+def rank_seed(rank: int, step: int) -> int:
+    """Seed of a rank's step: every rank simulates its own, disjoint histories."""
+    return 1_000_003 * (rank + 1) + 2 * step
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The timed region's length is the slowest rank's (barrier-bracketed)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def emit(obj):
     print(json.dumps(obj), flush=True)
 
@@ -190,7 +211,7 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 2x the 129 MB L2
 
     def step(i):
-        se = 1_000_003 * (rank + 1) + 2 * i
+        se = rank_seed(rank, i)
         ctx.plan_reset(plan_e, se, sh)
         ctx.run([plan_e], [N_E], sh)
         st_e = ctx.plan_result(plan_e, 0.5, out["de"].data_ptr(), out["se"].data_ptr(), sh)
@@ -218,11 +239,7 @@ def run_ours(args):
     if dist:
         dist.barrier()
     ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(ms), dist, dev)
     value = (N_E + N_G) * args.steps * world / (total_ms / 1e3)
 
     # end to end through the C ABI with host buffers: phantom upload, both
@@ -278,6 +295,142 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _c4_phantom(spec):
+    ph = spec.phantom()
+    return ph.dims, ph.voxel_cm, ph.mat, ph.rho
+
+
+def c4_phantoms(specs):
+    """The seeded C4 phantoms, generated over the host cores (spawned workers)."""
+    import multiprocessing as mp
+
+    import workloads as W
+    with mp.get_context("spawn").Pool(min(host_cores(), len(specs))) as pool:
+        parts = pool.map(_c4_phantom, specs)
+    return [W.Phantom(d, v, m, r) for d, v, m, r in parts]
+
+
+def run_batched(args):
+    """Config 4: 64 independent uneven plans in one batched persistent launch
+    (autotuned), against the same plans run one by one."""
+    import torch
+
+    import paper_1101_1245_gb300 as g
+    import workloads as W
+    from paper_1101_1245_gb300.autotune import autotune
+
+    specs = W.config4()
+    phantoms = c4_phantoms(specs)
+    ctx = g.engine(0)
+    pids = [ctx.create_phantom(ph) for ph in phantoms]
+    srcs = [W.square_field(sp.particle, sp.energy, ph, sp.field_cm) for sp, ph in zip(specs, phantoms)]
+    nh = [-(-sp.n_histories // 16) * 16 for sp in specs]  # whole multiples of the 16 batches
+    sample = [(pids[i], srcs[i], max(20_000, nh[i] // 50)) for i in range(0, len(specs), 4)]
+    tuned = autotune(ctx, sample)
+    plans = [ctx.plan_open(pid, src, sp.seed, 16) for pid, src, sp in zip(pids, srcs, specs)]
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+
+    def batched():
+        for p, sp in zip(plans, specs):
+            ctx.plan_reset(p, sp.seed)
+        torch.cuda.synchronize()
+        ev[0].record()
+        ctx.run(plans, nh)
+        st = [ctx.plan_result(p, 0.5) for p in plans]
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]), st
+
+    def plain():
+        tot = 0.0
+        for p, sp, n in zip(plans, specs, nh):
+            ctx.plan_reset(p, sp.seed)
+            torch.cuda.synchronize()
+            ev[0].record()
+            ctx.run([p], [n])
+            ctx.plan_result(p, 0.5)
+            ev[1].record()
+            torch.cuda.synchronize()
+            tot += ev[0].elapsed_time(ev[1])
+        return tot
+
+    for _ in range(max(1, args.warmup)):
+        batched()
+        plain()
+    tb = statistics.median([batched()[0] for _ in range(args.steps)])
+    tp = statistics.median([plain() for _ in range(args.steps)])
+    _, st = batched()
+    total = sum(nh)
+    emit({"workload": "c4_batched_64_plans", "metric": "histories/s (64 uneven plans, to FP64 dose + sigma)",
+          "unit": UNIT, "batched_value": total / (tb / 1e3), "plain_value": total / (tp / 1e3),
+          "batched_over_plain": tp / tb, "batched_ms": tb, "plain_ms": tp, "histories": total,
+          "plans": len(plans), "voxels": int(sum(ph.nvox for ph in phantoms)),
+          "electron_plans": int(sum(sp.particle for sp in specs)),
+          "ledger_exact": all(x["e_deposited"] + x["e_escaped"] + x["e_rest"] == x["e_incident"] for x in st),
+          "autotuned_launch": tuned["launch"], "autotune_trials": len(tuned["trials"]),
+          "n_batches": 16, "steps": args.steps, "data": "synthetic"})
+    ctx.close()
+
+
+def run_served(args):
+    """Config 5: a Poisson stream of dose requests from the config-4
+    distribution on resident phantoms, served with continuous batching to a
+    relative uncertainty target over voxels above 50% of D_max; against the
+    same requests run one by one."""
+    import numpy as np
+
+    import paper_1101_1245_gb300 as g
+    import workloads as W
+    from paper_1101_1245_gb300.serve import DoseRequest, Server, run_alone
+
+    pool_specs = W.config4()
+    phantoms = c4_phantoms(pool_specs)
+    budget = int(args.budget_gb * 2 ** 30)
+    ctx = g.engine(0, hbm_budget_bytes=budget + (8 << 30))
+    pids = [ctx.create_phantom(ph) for ph in phantoms]
+
+    def requests(rate):
+        reqs = []
+        for i, r in enumerate(W.config5(count=args.requests, rate_per_s=rate)):
+            k = i % len(phantoms)
+            ph, sp = phantoms[k], r.spec
+            src = W.square_field(sp.particle, sp.energy, ph, sp.field_cm)
+            reqs.append(DoseRequest(i, pids[k], ph.nvox, src, sp.seed, r.arrival_s, 400_000_000))
+        return reqs
+
+    # capacity: all of a calibration set at once
+    cal = requests(1.0)[:min(48, args.requests)]
+    srv = Server(ctx, budget, target=args.target)
+    for q in cal:
+        srv.submit(q)
+    srv.run(real_time=False)
+    rep_cal = srv.report()
+    mean_h = rep_cal["histories"] / max(rep_cal["requests"], 1)
+    rate = 0.8 * rep_cal["histories_per_s"] / mean_h
+    # the stream
+    srv = Server(ctx, budget, target=args.target)
+    reqs = requests(rate)
+    for q in reqs:
+        srv.submit(q)
+    srv.run(real_time=True)
+    rep = srv.report()
+    # the plain form on a sample of the same requests, one at a time
+    sample = reqs[:min(len(reqs), 40)]
+    alone = [run_alone(ctx, q, args.target) for q in sample]
+    alone_h = sum(a.histories for a in alone)
+    alone_t = sum(a.done_s for a in alone)
+    emit({"workload": "c5_served", "metric": "histories/s and request latency at s_0.5 <= target",
+          "unit": UNIT, "requests": rep["requests"], "target": args.target, "threshold": 0.5,
+          "arrival_rate_per_s": rate, "rate_basis": "0.8 x batched capacity measured on a calibration set",
+          "served_value": rep["histories_per_s"], "latency_p50_s": rep["latency_p50_s"],
+          "latency_p99_s": rep["latency_p99_s"], "wall_s": rep["wall_s"], "rounds": rep["rounds"],
+          "mean_histories_per_request": rep["histories"] / max(rep["requests"], 1),
+          "s_thr_max": rep["s_thr_max"], "alone_value": alone_h / alone_t if alone_t else None,
+          "alone_sample": len(sample), "hbm_budget_gb": args.budget_gb,
+          "phantoms": "64 resident config-4 phantoms, request i on phantom i mod 64", "data": "synthetic"})
+    ctx.close()
+
+
 def run_ncu_case():
     """Each beam of the step once at 1/5 of its histories, untimed: the small
     case profiled with ncu --set full (one launch of the transport kernel per beam)."""
@@ -303,6 +456,12 @@ def main():
     args = parse()
     if args.ncu_case:
         run_ncu_case()
+        return
+    if args.workload == "batched":
+        run_batched(args)
+        return
+    if args.workload == "served":
+        run_served(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -284,6 +284,37 @@ def simulate(mats, phys, ph, src, n_histories: int, seed: int, flags: int = 0,
     return OracleResult(n_histories, s1, s2, st, time.perf_counter() - t0, procs)
 
 
+def simulate_parts(mats, phys, ph, src, n_histories: int, seed: int, parts: int,
+                   processes: int = 1, flags: int = 0):
+    """Histories [0, n) split into `parts` equal, independent ranges (for
+    sample-variance estimates of any aggregate), run over one pool of spawned
+    workers.  Returns one OracleResult per part."""
+    import multiprocessing as mp
+    import time
+
+    t0 = time.perf_counter()
+    cuts = np.linspace(0, n_histories, parts + 1).astype(np.int64)
+    per_part = max(1, processes // parts)
+    jobs, owner = [], []
+    for i in range(parts):
+        sub = np.linspace(cuts[i], cuts[i + 1], per_part + 1).astype(np.int64)
+        for j in range(per_part):
+            if sub[j + 1] > sub[j]:
+                jobs.append((mats, phys, ph, src, int(sub[j]), int(sub[j + 1]), seed, flags))
+                owner.append(i)
+    with mp.get_context("spawn").Pool(max(1, min(processes, len(jobs)))) as pool:
+        outs = pool.map(_worker, jobs)
+    res = []
+    for i in range(parts):
+        mine = [o for o, k in zip(outs, owner) if k == i]
+        s1 = sum(o[0] for o in mine)
+        s2 = sum(o[1] for o in mine)
+        st = {k: sum(o[2][k] for o in mine) for k in mine[0][2]}
+        res.append(OracleResult(int(cuts[i + 1] - cuts[i]), s1, s2, st,
+                                time.perf_counter() - t0, processes))
+    return res
+
+
 def first_interaction_z(mats, phys, ph, src, n: int, seed: int):
     L = lib()
     keep = _Keep()

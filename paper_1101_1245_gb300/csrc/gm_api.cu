@@ -658,13 +658,8 @@ gpumcd_status gpumcd_plan_result(gpumcd_ctx *c, int32_t plan_id, double thr, dou
     double *dsig = sigma ? sigma : tsig;
     double h_nb[64] = {0};
     const uint64_t N = p.hist_done;
-    const uint64_t cyc = 32ull * p.W;
-    for (uint32_t b = 0; b < p.W; ++b) {
-        const uint64_t full = N / cyc, rem = N % cyc;
-        uint64_t extra = rem > 32ull * b ? rem - 32ull * b : 0;
-        if (extra > 32) extra = 32;
-        h_nb[b] = (double)(32ull * full + extra);
-    }
+    // history h belongs to batch h mod W
+    for (uint32_t b = 0; b < p.W; ++b) h_nb[b] = (double)(N / p.W + (b < N % p.W ? 1u : 0u));
     CK(cudaMemsetAsync(red, 0, 64, s));
     const double inv_vol = 1.0 / (ph.voxel[0] * ph.voxel[1] * ph.voxel[2]);
     if (N > 0) {
@@ -711,13 +706,8 @@ gpumcd_status gpumcd_plan_result_noalloc(gpumcd_ctx *c, int32_t plan_id, double 
     ST(set_device(c));
     cudaStream_t s = pick(c, stream);
     double h_nb[64] = {0};
-    const uint64_t cyc = 32ull * p.W;
-    for (uint32_t b = 0; b < p.W; ++b) {
-        const uint64_t full = N / cyc, rem = N % cyc;
-        uint64_t extra = rem > 32ull * b ? rem - 32ull * b : 0;
-        if (extra > 32) extra = 32;
-        h_nb[b] = (double)(32ull * full + extra);
-    }
+    // history h belongs to batch h mod W
+    for (uint32_t b = 0; b < p.W; ++b) h_nb[b] = (double)(N / p.W + (b < N % p.W ? 1u : 0u));
     unsigned long long res[4] = {0, 0, 0, 0}, led[4] = {0, 0, 0, 0};
     const double inv_vol = 1.0 / (ph.voxel[0] * ph.voxel[1] * ph.voxel[2]);
     CK(launch_fold_noalloc(c->device, (const unsigned long long *)p.tally.p, (const uint32_t *)ph.vox.p, ph.nvox,

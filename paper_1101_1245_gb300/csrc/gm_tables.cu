@@ -341,6 +341,81 @@ __global__ void k_fold(const unsigned long long *tally, const uint32_t *vox, uin
     }
 }
 
+// The same fold for equal batches (n_b = N / W for every b): the variance
+// numerator is formed exactly in 128-bit integers,
+//   sum_b (S_b - S/W)^2 = (W sum_b S_b^2 - S^2) / W,
+// so only one conversion to FP64 per voxel remains (FP64 is scarce on GB300
+// and the per-batch FP64 work of k_fold bounds it).  A voxel whose sums would
+// not fit 128 bits (sum S_b^2 >= 2^121, far beyond realistic tallies) takes
+// the FP64 two-pass form instead.
+struct U128 {
+    unsigned long long lo, hi;
+};
+
+__device__ __forceinline__ void add_sq(U128 &acc, unsigned long long x) {
+    const unsigned long long lo = x * x, hi = __umul64hi(x, x);
+    const unsigned long long nl = acc.lo + lo;
+    acc.hi += hi + (nl < lo ? 1ull : 0ull);
+    acc.lo = nl;
+}
+
+__device__ __forceinline__ double u128_to_double(U128 v) {
+    return (double)v.hi * 18446744073709551616.0 + (double)v.lo;
+}
+
+template <int W>
+__global__ void k_fold_equal(const unsigned long long *tally, const uint32_t *vox, uint64_t nvox, double n_tot,
+                             double inv_vol, double *dose, double *sigma, unsigned long long *dmax_bits,
+                             unsigned long long *dep_sum) {
+    double local_max = 0.0;
+    unsigned long long local_sum = 0;
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < nvox;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        unsigned long long s[W];
+        unsigned long long tot = 0;
+        U128 sq{0ull, 0ull};
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            s[b] = __ldcs(tally + (uint64_t)b * nvox + v);
+            tot += s[b];
+            add_sq(sq, s[b]);
+        }
+        const double mean = (double)tot / n_tot;
+        const double n = n_tot / (double)W;
+        double var;
+        if (sq.hi < (1ull << 57)) {
+            // W sum S_b^2 - S^2, exact and non-negative (Cauchy-Schwarz); then
+            // var(D) = sum_b (S_b - S/W)^2 / (W (W - 1) n^2) = num / (W^2 (W - 1) n^2)
+            const U128 ws{sq.lo * (unsigned long long)W, sq.hi * (unsigned long long)W + __umul64hi(sq.lo, (unsigned long long)W)};
+            const U128 t2{tot * tot, __umul64hi(tot, tot)};
+            const U128 num{ws.lo - t2.lo, ws.hi - t2.hi - (ws.lo < t2.lo ? 1ull : 0ull)};
+            var = u128_to_double(num) / ((double)W * (double)W * (double)(W - 1) * n * n);
+        } else {
+            double acc = 0.0;
+            for (int b = 0; b < W; ++b) {
+                const double t = fma(-n, mean, (double)s[b]);
+                acc = fma(t, t, acc);
+            }
+            var = acc * ((double)W / ((double)(W - 1) * n_tot * n_tot));
+        }
+        const double rho = (double)(vox[v] >> 4) * (double)kRhoQ;
+        const double scale = kQ * kMeVPerGramToGy * inv_vol / rho;
+        const double dv = mean * scale;
+        if (dose) dose[v] = dv;
+        if (sigma) sigma[v] = sqrt(var) * scale;
+        local_max = fmax(local_max, dv);
+        local_sum += tot;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        local_max = fmax(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
+        local_sum += __shfl_xor_sync(0xffffffffu, local_sum, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(dmax_bits, (unsigned long long)__double_as_longlong(local_max));
+        if (local_sum) atomicAdd(dep_sum, local_sum);
+    }
+}
+
 // s_thr = mean of sigma/D over voxels with D > thr * D_max (GPUMCD §II.D, s).
 __global__ void k_sthr(const double *dose, const double *sigma, uint64_t nvox,
                        const unsigned long long *dmax_bits, double thr, double *sum,
@@ -452,10 +527,24 @@ cudaError_t launch_fold(const unsigned long long *tally, const uint32_t *vox, ui
                         const double *n_b, double n_tot, double inv_vol, double *dose, double *sigma,
                         unsigned long long *dmax_bits, unsigned long long *dep_sum, int n_sm, cudaStream_t s) {
     FoldArgs fa;
-    for (int b = 0; b < 64; ++b) fa.n_b[b] = b < W ? n_b[b] : 0.0;
+    bool equal = true;
+    for (int b = 0; b < 64; ++b) {
+        fa.n_b[b] = b < W ? n_b[b] : 0.0;
+        if (b < W && n_b[b] != n_b[0]) equal = false;
+    }
     uint64_t blocks = (nvox + 255) / 256;
     const uint64_t cap = (uint64_t)n_sm * 8;
     const int grid = (int)(blocks < cap ? (blocks ? blocks : 1) : cap);
+    if (equal) {
+        switch (W) {
+            case 8: k_fold_equal<8><<<grid, 256, 0, s>>>(tally, vox, nvox, n_tot, inv_vol, dose, sigma, dmax_bits, dep_sum); break;
+            case 16: k_fold_equal<16><<<grid, 256, 0, s>>>(tally, vox, nvox, n_tot, inv_vol, dose, sigma, dmax_bits, dep_sum); break;
+            case 32: k_fold_equal<32><<<grid, 256, 0, s>>>(tally, vox, nvox, n_tot, inv_vol, dose, sigma, dmax_bits, dep_sum); break;
+            case 64: k_fold_equal<64><<<grid, 256, 0, s>>>(tally, vox, nvox, n_tot, inv_vol, dose, sigma, dmax_bits, dep_sum); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (W) {
         case 8: k_fold<8><<<grid, 256, 0, s>>>(tally, vox, nvox, fa, n_tot, inv_vol, dose, sigma, dmax_bits, dep_sum); break;
         case 16: k_fold<16><<<grid, 256, 0, s>>>(tally, vox, nvox, fa, n_tot, inv_vol, dose, sigma, dmax_bits, dep_sum); break;

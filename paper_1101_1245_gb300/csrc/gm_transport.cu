@@ -107,7 +107,7 @@ __device__ __forceinline__ void red_add_u64(unsigned long long *addr, unsigned l
 
 __device__ __forceinline__ void deposit(const PlanDev &P, uint32_t hist, uint32_t idx, uint32_t e) {
     if (e == 0u) return;
-    const uint32_t b = (hist >> 5) & P.bmask;
+    const uint32_t b = hist & P.bmask;  // batch = history mod W
     red_add_u64(P.tally + (size_t)b * P.nvox + idx, (unsigned long long)e);
 }
 
@@ -119,7 +119,7 @@ __device__ __forceinline__ void deposit_aggregated(const PlanDev &P, uint32_t hi
     const bool on = e != 0u;
     const unsigned mask = __ballot_sync(FULL, on);
     if (!on) return;
-    const uint32_t b = (hist >> 5) & P.bmask;
+    const uint32_t b = hist & P.bmask;  // batch = history mod W
     unsigned long long *addr = P.tally + (size_t)b * P.nvox + idx;
     const unsigned peers = __match_any_sync(mask, (unsigned long long)addr);
     const unsigned lo = __reduce_add_sync(peers, e & 0xFFFFu);

@@ -1,0 +1,115 @@
+"""Batched and served forms: several plans in one persistent launch give each
+plan the same tally, bit for bit, as running it alone; the autotuner changes
+speed, not results; the server retires requests at the uncertainty target,
+admits them within its HBM budget, and a served result equals the same
+request rerun alone at the same history count."""
+import numpy as np
+import pytest
+
+import paper_1101_1245_gb300 as g
+import workloads as W
+from tests.gpu_common import make_ctx
+
+pytestmark = pytest.mark.gpu
+
+
+def _specs(count=6, seed=44):
+    return W.plan_distribution(count, seed, n_lo=24, n_hi=40, hist_lo=2e4, hist_hi=6e4)
+
+
+def _setup(ctx, specs):
+    phantoms = [sp.phantom() for sp in specs]
+    pids = [ctx.create_phantom(ph) for ph in phantoms]
+    srcs = [W.square_field(sp.particle, sp.energy, ph, sp.field_cm) for sp, ph in zip(specs, phantoms)]
+    return phantoms, pids, srcs
+
+
+def _dose(ctx, plan, nvox):
+    import torch
+    d = torch.zeros(nvox, dtype=torch.float64, device="cuda")
+    s = torch.zeros(nvox, dtype=torch.float64, device="cuda")
+    st = ctx.plan_result(plan, 0.5, d.data_ptr(), s.data_ptr())
+    return d.cpu().numpy(), s.cpu().numpy(), st
+
+
+def test_batched_launch_equals_plans_alone():
+    ctx = make_ctx()
+    specs = _specs()
+    assert {sp.particle for sp in specs} == {W.PHOTON, W.ELECTRON}
+    phantoms, pids, srcs = _setup(ctx, specs)
+    n = [sp.n_histories for sp in specs]
+    mix = [ctx.plan_open(pid, src, sp.seed, 16) for pid, src, sp in zip(pids, srcs, specs)]
+    ctx.run(mix, n)
+    for i, (pid, src, sp) in enumerate(zip(pids, srcs, specs)):
+        alone = ctx.plan_open(pid, src, sp.seed, 16)
+        ctx.run([alone], [n[i]])
+        a = _dose(ctx, alone, phantoms[i].nvox)
+        b = _dose(ctx, mix[i], phantoms[i].nvox)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        for k in ("e_incident", "e_deposited", "e_escaped", "e_rest"):
+            assert a[2][k] == b[2][k]
+        assert b[2]["e_deposited"] + b[2]["e_escaped"] + b[2]["e_rest"] == b[2]["e_incident"]
+        ctx.plan_close(alone)
+    ctx.close()
+
+
+def test_autotune_changes_speed_not_results():
+    from paper_1101_1245_gb300.autotune import autotune
+    ctx = make_ctx()
+    specs = _specs(4, seed=45)
+    phantoms, pids, srcs = _setup(ctx, specs)
+    p0 = ctx.plan_open(pids[0], srcs[0], 7, 16)
+    ctx.run([p0], [30_000])
+    before = _dose(ctx, p0, phantoms[0].nvox)
+    res = autotune(ctx, [(pid, src, 10_000) for pid, src in zip(pids, srcs)], reps=1)
+    assert res["transport_ms"] > 0 and len(res["trials"]) >= 4
+    assert ctx.get_launch()["block_threads"] == res["launch"]["block_threads"]
+    p1 = ctx.plan_open(pids[0], srcs[0], 7, 16)
+    ctx.run([p1], [30_000])
+    after = _dose(ctx, p1, phantoms[0].nvox)
+    assert np.array_equal(before[0], after[0])
+    ctx.close()
+
+
+def test_served_results_equal_alone_reruns():
+    from paper_1101_1245_gb300.serve import DoseRequest, Server
+    ctx = make_ctx()
+    specs = _specs(6, seed=46)
+    phantoms, pids, srcs = _setup(ctx, specs)
+    srv = Server(ctx, hbm_budget=8 << 30, target=0.05, round_histories=300_000,
+                 first_chunk=20_000, keep_dose=True)
+    for i, (pid, src, sp) in enumerate(zip(pids, srcs, specs)):
+        srv.submit(DoseRequest(i, pid, phantoms[i].nvox, src, sp.seed, 0.0, 3_000_000))
+    results = {r.rid: r for r in srv.run(real_time=False)}
+    assert len(results) == 6
+    assert all(r.s_thr <= 0.05 or r.histories >= 3_000_000 for r in results.values())
+    assert srv.report()["latency_p99_s"] >= srv.report()["latency_p50_s"] > 0
+    for i in (0, 3):
+        r = results[i]
+        plan = ctx.plan_open(pids[i], srcs[i], specs[i].seed, 16)
+        first = r.histories // 3
+        ctx.run([plan], [first])
+        ctx.run([plan], [r.histories - first])
+        d, s, _ = _dose(ctx, plan, phantoms[i].nvox)
+        assert np.array_equal(d, r.dose) and np.array_equal(s, r.sigma)
+        ctx.plan_close(plan)
+    ctx.close()
+
+
+def test_server_admits_within_budget():
+    from paper_1101_1245_gb300.serve import DoseRequest, Server
+    ctx = make_ctx()
+    specs = _specs(5, seed=47)
+    phantoms, pids, srcs = _setup(ctx, specs)
+    biggest = max(16 * ph.nvox * 8 + 64 for ph in phantoms)
+    srv = Server(ctx, hbm_budget=2 * biggest, target=0.08, round_histories=200_000,
+                 first_chunk=20_000)
+    for i, (pid, src, sp) in enumerate(zip(pids, srcs, specs)):
+        srv.submit(DoseRequest(i, pid, phantoms[i].nvox, src, sp.seed, 0.0, 2_000_000))
+    assert len(srv.run(real_time=False)) == 5
+    assert srv.max_used <= 2 * biggest and srv.used == 0
+    assert srv.max_active < 5  # the budget held some requests back
+    tiny = Server(ctx, hbm_budget=1024, target=0.08)
+    with pytest.raises(g.GpumcdError):
+        tiny.submit(DoseRequest(9, pids[0], phantoms[0].nvox, srcs[0], 1, 0.0))
+    ctx.close()

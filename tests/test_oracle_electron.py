@@ -217,3 +217,11 @@ def test_history_split_is_exact():
     b2 = oracle.simulate(W.MATERIALS, P, pl.phantom, pl.source, 250, 1, hist_begin=150)
     assert np.allclose(a.sum_e, b1.sum_e + b2.sum_e, rtol=1e-12, atol=1e-12)
     assert np.allclose(a.sum_e2, b1.sum_e2 + b2.sum_e2, rtol=1e-12, atol=1e-12)
+
+
+def test_parts_add_up_to_the_whole_run():
+    pl = W.config1(n_histories=300)
+    whole = oracle.simulate(W.MATERIALS, P, pl.phantom, pl.source, 300, 1)
+    parts = oracle.simulate_parts(W.MATERIALS, P, pl.phantom, pl.source, 300, 1, parts=3, processes=3)
+    assert [p.n_histories for p in parts] == [100, 100, 100]
+    assert np.allclose(sum(p.sum_e for p in parts), whole.sum_e, rtol=1e-12, atol=1e-12)
