@@ -201,6 +201,7 @@ const char *gpumcd_status_string(gpumcd_status s) {
         case GPUMCD_ERR_NOT_FOUND: return "unknown id";
         case GPUMCD_ERR_BUDGET: return "HBM budget exceeded";
         case GPUMCD_ERR_STATE: return "call out of order";
+        case GPUMCD_ERR_CORRUPT: return "device state check failed";
         default: return "unknown status";
     }
 }
@@ -296,6 +297,7 @@ gpumcd_status gpumcd_load_materials(gpumcd_ctx *c, const gpumcd_material *mats, 
     c->dphys.p_cut_q = (uint32_t)std::llround(ph->p_cut / kQ);
     c->dphys.e_abs_q = (uint32_t)std::llround(ph->e_abs / kQ);
     c->dphys.two_mc2_q = (uint32_t)std::llround(2.0 * kMC2 / kQ);
+    c->dphys.e_max_q = (uint32_t)std::llround(ph->e_max / kQ);
     c->dphys.t_c = (float)ph->t_c;
     c->dphys.k_c = (float)ph->k_c;
     c->dphys.estepe = (float)ph->estepe;

@@ -52,7 +52,7 @@ struct Grid {
 
 // Transport parameters in device form.
 struct Phys {
-    uint32_t p_cut_q, e_abs_q, two_mc2_q;
+    uint32_t p_cut_q, e_abs_q, two_mc2_q, e_max_q;
     float t_c, k_c, estepe, nudge;
     Grid grid;
 };

@@ -181,6 +181,20 @@ __device__ __forceinline__ void load_rec(Lane &p, const Rec &r) {
     p.act = true;
 }
 
+// A record whose plan index or energy is out of range is dropped and
+// reported (GPUMCD_ERR_CORRUPT) instead of being transported: every later
+// plan and tally access is indexed through the plan field.  (E may be 0: an
+// electron whose whole energy went to a bremsstrahlung photon; E may exceed
+// e_max by the FP32 rounding of a spectrum's top edge, hence the margin.)
+__device__ __forceinline__ void load_checked(const TransportArgs &A, Lane &p, const Rec &r) {
+    load_rec(p, r);
+    if (p.plan >= (uint32_t)A.n_plans || p.E > A.phys.e_max_q + (A.phys.e_max_q >> 8)) {
+        atomicExch(A.error, GPUMCD_ERR_CORRUPT);
+        p.act = false;
+        p.plan = 0u;
+    }
+}
+
 __device__ __forceinline__ Rec make_rec(const Lane &p) {
     Rec r;
     r.a = make_float4(p.x, p.y, p.z, p.ux);
@@ -364,6 +378,11 @@ __device__ void photon_event(const TransportArgs &A, const Smem &S, Lane &p, int
     const uint32_t idx = voxel_index(P, p.x, p.y, p.z, ix, iy, iz);
     const uint32_t vw = __ldg(P.vox + idx);
     const int m = vw & 15u;
+    if (m >= NMAT) {
+        atomicExch(A.error, GPUMCD_ERR_CORRUPT);
+        p.act = false;
+        return;
+    }
     const float rho = (float)(vw >> 4) * kRhoQ;
     const float *tp = S.tab + TAB_PH + m * 3 * G;
     const bool pair_open = p.E > ph.two_mc2_q;
@@ -473,6 +492,11 @@ __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, in
     const uint32_t idx0 = voxel_index(P, p.x, p.y, p.z, ix, iy, iz);
     const uint32_t vw = __ldg(P.vox + idx0);
     const int m0 = vw & 15u;
+    if (m0 >= NMAT) {
+        atomicExch(A.error, GPUMCD_ERR_CORRUPT);
+        p.act = false;
+        return false;
+    }
     const float rho0 = (float)(vw >> 4) * kRhoQ;
     if (p.E < ph.e_abs_q) {
         deposit(P, p.hist, idx0, p.E);
@@ -536,6 +560,11 @@ __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, in
     // electron Woodcock: accept a real hard event with Sigma(end)/Sigma_hat(start)
     const uint32_t vw1 = __ldg(P.vox + idx1);
     const int m1 = vw1 & 15u;
+    if (m1 >= NMAT) {
+        atomicExch(A.error, GPUMCD_ERR_CORRUPT);
+        p.act = false;
+        return true;
+    }
     const float rho1 = (float)(vw1 >> 4) * kRhoQ;
     const float *t1 = S.tab + TAB_EL + m1 * 4 * G;
     const float xe1 = fmaf(__log2f((float)e1), ph.grid.el_a, ph.grid.el_bq);
@@ -660,7 +689,7 @@ __device__ int refill(const TransportArgs &A, const Smem &S, CtaFlags &F, Lane &
         if (take) {
             const unsigned rank = __popc(empty & lt);
             if (!p.act && rank < take)
-                load_rec(p, A.stacks[((size_t)gw * 2 + t) * A.stack_cap + (sc - 1u - rank)]);
+                load_checked(A, p, A.stacks[((size_t)gw * 2 + t) * A.stack_cap + (sc - 1u - rank)]);
             __syncwarp();
             if (lane == 0) ws.stk[t] = sc - take;
             __syncwarp();
@@ -683,7 +712,7 @@ __device__ int refill(const TransportArgs &A, const Smem &S, CtaFlags &F, Lane &
         }
         const unsigned take = (unsigned)min((unsigned long long)__popc(empty), hi - lo);
         const unsigned rank = __popc(empty & lt);
-        if (!p.act && rank < take) load_rec(p, A.in[t].rec[lo + rank]);
+        if (!p.act && rank < take) load_checked(A, p, A.in[t].rec[lo + rank]);
         __syncwarp();
         if (lane == 0) {
             ws.q_lo[t] = lo + take;
