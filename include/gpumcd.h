@@ -48,6 +48,7 @@ typedef int32_t gpumcd_status;
 #define GPUMCD_MAX_MATERIALS 4
 #define GPUMCD_MAX_ELEMENTS 16
 #define GPUMCD_MAX_PLANS_PER_RUN 64
+#define GPUMCD_MAX_INFLIGHT 2        /* launch sequences gpumcd_submit keeps in flight at once */
 #define GPUMCD_MAX_SPECTRUM_BINS 1024
 
 #define GPUMCD_PHOTON 0
@@ -202,6 +203,34 @@ gpumcd_status gpumcd_plan_reset(gpumcd_ctx *ctx, int32_t plan_id, uint64_t seed,
 gpumcd_status gpumcd_run(gpumcd_ctx *ctx, int32_t n_plans, const int32_t *plan_ids,
                          const uint64_t *n_histories, void *stream);
 
+/* Asynchronous gpumcd_run, for continuous batching (a serving step of the
+ * paper's history loop, §II.C, with no counterpart of its own there).  Enqueues
+ * the sequence's first launch and returns a ticket at once.  Each of the
+ * GPUMCD_MAX_INFLIGHT sequences has its own scratch and its own low-priority
+ * stream.  That stream waits for the work already enqueued on the context's
+ * stream; work the caller enqueued on other streams must be ordered by the
+ * caller.
+ *
+ * Sequences in flight overlap on the device.  The CTAs of one fill the SMs
+ * that the other's drain frees.  A plan may be in several sequences at once.
+ * Its histories are numbered in submission order, and the tally is an integer
+ * sum, so the result does not depend on the overlap.  While a plan is in a
+ * sequence that has not finished, gpumcd_plan_result, _noalloc, _reset and
+ * _close return GPUMCD_ERR_STATE.  A sequence that fails marks its plans
+ * failed: their results return GPUMCD_ERR_STATE until gpumcd_plan_reset.
+ * With all slots busy, the call returns GPUMCD_ERR_STATE. */
+gpumcd_status gpumcd_submit(gpumcd_ctx *ctx, int32_t n_plans, const int32_t *plan_ids,
+                            const uint64_t *n_histories, int32_t *ticket);
+
+/* Without blocking: *done = 0 while the ticket's first launch runs.  Else it
+ * finishes the sequence as gpumcd_wait does (including any relaunches over
+ * the overflow queues), sets *done = 1 and returns the sequence's status.  A
+ * ticket that is finished or unknown returns GPUMCD_ERR_NOT_FOUND. */
+gpumcd_status gpumcd_poll(gpumcd_ctx *ctx, int32_t ticket, int32_t *done);
+
+/* Blocks until the ticket's sequence has finished; returns its status. */
+gpumcd_status gpumcd_wait(gpumcd_ctx *ctx, int32_t ticket);
+
 /* FP64 fold of a plan's tally (§II.D): dose and sigma in Gy per history into
  * device arrays of nx*ny*nz doubles (either may be NULL), plus stats with
  * s_thr over voxels with dose > threshold_frac * D_max. */
@@ -209,7 +238,7 @@ gpumcd_status gpumcd_plan_result(gpumcd_ctx *ctx, int32_t plan_id, double thresh
                                  double *dose_out, double *sigma_out, void *stream,
                                  gpumcd_run_stats *stats);
 
-/* Histories simulated so far by a plan. */
+/* Histories of a plan's finished sequences. */
 gpumcd_status gpumcd_plan_histories(gpumcd_ctx *ctx, int32_t plan_id, uint64_t *histories);
 
 /* Device bytes the context currently holds, and its budget. */

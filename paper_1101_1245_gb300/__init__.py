@@ -22,6 +22,7 @@ LIB_PATH = _build.LIB
 MAX_MATERIALS = 4
 MAX_ELEMENTS = 16
 MAX_PLANS_PER_RUN = 64
+MAX_INFLIGHT = 2
 ENERGY_QUANTUM_MEV = 1.0 / 67108864.0
 PHOTON, ELECTRON = 0, 1
 BEAM_PENCIL, BEAM_SQUARE = 0, 1
@@ -115,6 +116,9 @@ SIGNATURES = {
     "gpumcd_plan_close": (_ST, [_CTX, _I32]),
     "gpumcd_plan_reset": (_ST, [_CTX, _I32, _U64, _P]),
     "gpumcd_run": (_ST, [_CTX, _I32, C.POINTER(_I32), C.POINTER(_U64), _P]),
+    "gpumcd_submit": (_ST, [_CTX, _I32, C.POINTER(_I32), C.POINTER(_U64), C.POINTER(_I32)]),
+    "gpumcd_poll": (_ST, [_CTX, _I32, C.POINTER(_I32)]),
+    "gpumcd_wait": (_ST, [_CTX, _I32]),
     "gpumcd_plan_result": (_ST, [_CTX, _I32, _D, _P, _P, _P, C.POINTER(RunStats)]),
     "gpumcd_plan_histories": (_ST, [_CTX, _I32, C.POINTER(_U64)]),
     "gpumcd_plan_result_noalloc": (_ST, [_CTX, _I32, _D, _P, _P, _P, C.POINTER(RunStats)]),
@@ -298,6 +302,23 @@ class Context:
         ids = (_I32 * len(plans))(*plans)
         ns = (_U64 * len(plans))(*n_histories)
         _check(self._L.gpumcd_run(self.h, len(plans), ids, ns, stream or None), "gpumcd_run")
+
+    def submit(self, plans: Sequence[int], n_histories: Sequence[int]) -> int:
+        """Asynchronous run: enqueues the launch sequence and returns its ticket."""
+        ids = (_I32 * len(plans))(*plans)
+        ns = (_U64 * len(plans))(*n_histories)
+        t = _I32()
+        _check(self._L.gpumcd_submit(self.h, len(plans), ids, ns, C.byref(t)), "gpumcd_submit")
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        """True once the ticket's sequence has finished (raising on its failure)."""
+        d = _I32()
+        _check(self._L.gpumcd_poll(self.h, ticket, C.byref(d)), "gpumcd_poll")
+        return bool(d.value)
+
+    def wait(self, ticket: int) -> None:
+        _check(self._L.gpumcd_wait(self.h, ticket), "gpumcd_wait")
 
     def plan_result(self, plan: int, threshold: float = 0.5, dose_ptr: int = 0,
                     sigma_ptr: int = 0, stream: int = 0) -> dict:

@@ -35,7 +35,10 @@ struct Plan {
     int32_t n_spec;
     uint64_t seed;
     uint32_t W;
-    uint64_t hist_done;
+    uint64_t hist_sub = 0;   // histories handed to launch sequences (numbering of the next run)
+    uint64_t hist_done = 0;  // histories of completed sequences (what a fold sees)
+    int inflight = 0;        // unfinished sequences that include this plan
+    bool failed = false;     // a sequence failed: the tally is incomplete until plan_reset
     DevBuf tally;   // [W][nvox] u64
     DevBuf ledger;  // [4] u64
     DevBuf spec;    // [2(n_spec+1)] floats
@@ -49,6 +52,27 @@ struct Control {
     unsigned long long counters[CNT_N];
     int32_t error;
     int32_t pad;
+};
+
+// Scratch and state of one launch sequence (the persistent kernel, then
+// relaunches over the overflow queues until they are empty).  Slot 0 serves
+// gpumcd_run on the caller's stream; slots 1..GPUMCD_MAX_INFLIGHT serve
+// gpumcd_submit on their own streams, so sequences can overlap on the device.
+struct Slot {
+    DevBuf stacks, queue[2][NT], control, plandev;
+    Control *h_control = nullptr;  // pinned: the control block after each launch
+    PlanDev *h_plandev = nullptr;  // pinned: the sequence's plan table
+    cudaStream_t own = nullptr;    // the slot's stream (asynchronous slots)
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, done = nullptr;
+    bool busy = false;
+    int32_t ticket = 0;
+    cudaStream_t s = nullptr;  // the stream the sequence runs on
+    TransportArgs A;
+    int grid = 0, block = 0, bps = 0;
+    uint32_t k = 0;  // launches enqueued
+    unsigned long long in_count[NT] = {0, 0};
+    std::vector<int32_t> ids;
+    std::vector<uint64_t> n_hist;
 };
 
 }  // namespace
@@ -68,11 +92,12 @@ struct gpumcd_ctx {
     std::map<int32_t, Plan> plans;
     int32_t next_id = 1;
     gpumcd_launch launch{};
-    // scratch of the launch sequence
-    DevBuf stacks, queue[2][NT], control, plandev, fold_tmp;
-    size_t fold_nvox = 0;
-    Control *h_control = nullptr;  // pinned
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    Slot slot[1 + GPUMCD_MAX_INFLIGHT];
+    Control last{};          // control block of the last finished sequence
+    bool have_last = false;
+    cudaEvent_t order = nullptr;  // orders a submitted sequence after the context stream
+    int32_t next_ticket = 1;
+    DevBuf fold_tmp;
     bool configured = false;
 };
 
@@ -152,20 +177,46 @@ bool valid_source(const gpumcd_ctx *c, const gpumcd_source *s) {
     return tot > 0.0 && s->spectrum_edges[0] > 0.0 && s->spectrum_edges[s->n_spectrum] <= c->phys.e_max;
 }
 
-gpumcd_status ensure_scratch(gpumcd_ctx *c, int grid, int block) {
+gpumcd_status ensure_slot(gpumcd_ctx *c, Slot &sl, int grid, int block) {
     const size_t warps = (size_t)grid * (block / 32);
-    ST(dev_alloc(c, c->stacks, warps * NT * c->launch.stack_capacity * sizeof(Rec)));
+    ST(dev_alloc(c, sl.stacks, warps * NT * c->launch.stack_capacity * sizeof(Rec)));
     for (int b = 0; b < 2; ++b)
         for (int t = 0; t < NT; ++t)
-            ST(dev_alloc(c, c->queue[b][t], (size_t)c->launch.overflow_capacity * sizeof(Rec)));
-    ST(dev_alloc(c, c->control, sizeof(Control)));
-    ST(dev_alloc(c, c->plandev, sizeof(PlanDev) * GPUMCD_MAX_PLANS_PER_RUN));
-    if (!c->h_control) CK(cudaMallocHost(&c->h_control, sizeof(Control)));
+            ST(dev_alloc(c, sl.queue[b][t], (size_t)c->launch.overflow_capacity * sizeof(Rec)));
+    ST(dev_alloc(c, sl.control, sizeof(Control)));
+    ST(dev_alloc(c, sl.plandev, sizeof(PlanDev) * GPUMCD_MAX_PLANS_PER_RUN));
+    if (!sl.h_control) CK(cudaMallocHost(&sl.h_control, sizeof(Control)));
+    if (!sl.h_plandev) CK(cudaMallocHost(&sl.h_plandev, sizeof(PlanDev) * GPUMCD_MAX_PLANS_PER_RUN));
+    if (!sl.ev0) CK(cudaEventCreate(&sl.ev0));
+    if (!sl.ev1) CK(cudaEventCreate(&sl.ev1));
+    if (!sl.done) CK(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
     if (!c->configured) {
         CK(transport_configure(block));
         c->configured = true;
     }
     return GPUMCD_OK;
+}
+
+void free_slot(gpumcd_ctx *c, Slot &sl) {
+    if (sl.busy && sl.s) cudaStreamSynchronize(sl.s);
+    dev_free(c, sl.stacks);
+    for (int b = 0; b < 2; ++b)
+        for (int t = 0; t < NT; ++t) dev_free(c, sl.queue[b][t]);
+    dev_free(c, sl.control);
+    dev_free(c, sl.plandev);
+    if (sl.h_control) cudaFreeHost(sl.h_control);
+    if (sl.h_plandev) cudaFreeHost(sl.h_plandev);
+    if (sl.ev0) cudaEventDestroy(sl.ev0);
+    if (sl.ev1) cudaEventDestroy(sl.ev1);
+    if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.own) cudaStreamDestroy(sl.own);
+    sl = Slot{};
+}
+
+bool any_busy(const gpumcd_ctx *c) {
+    for (const Slot &sl : c->slot)
+        if (sl.busy) return true;
+    return false;
 }
 
 }  // namespace
@@ -220,9 +271,13 @@ gpumcd_status gpumcd_init(gpumcd_ctx **out, int32_t device, uint64_t hbm_budget_
     c->budget = hbm_budget_bytes;
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
-    if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    // The context stream (tables, phantoms, folds, gpumcd_run by default) has
+    // the highest priority, so a fold takes SMs first as a submitted
+    // transport sequence drains; submitted sequences run at the lowest.
+    int least = 0, greatest = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->stream, cudaStreamNonBlocking, greatest);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->order, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         delete c;
         return cuda_status(e);
@@ -243,6 +298,8 @@ gpumcd_status gpumcd_destroy(gpumcd_ctx *c) {
     if (!c) return GPUMCD_OK;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    for (Slot &sl : c->slot)
+        if (sl.busy && sl.s) cudaStreamSynchronize(sl.s);
     for (auto &kv : c->plans) {
         dev_free(c, kv.second.tally);
         dev_free(c, kv.second.ledger);
@@ -254,15 +311,9 @@ gpumcd_status gpumcd_destroy(gpumcd_ctx *c) {
         dev_free(c, kv.second.maj);
     }
     dev_free(c, c->tab);
-    dev_free(c, c->stacks);
-    for (int b = 0; b < 2; ++b)
-        for (int t = 0; t < NT; ++t) dev_free(c, c->queue[b][t]);
-    dev_free(c, c->control);
-    dev_free(c, c->plandev);
+    for (Slot &sl : c->slot) free_slot(c, sl);
     dev_free(c, c->fold_tmp);
-    if (c->h_control) cudaFreeHost(c->h_control);
-    if (c->ev0) cudaEventDestroy(c->ev0);
-    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->order) cudaEventDestroy(c->order);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return GPUMCD_OK;
@@ -462,6 +513,7 @@ gpumcd_status gpumcd_plan_close(gpumcd_ctx *c, int32_t plan_id) {
     if (!c) return GPUMCD_ERR_INVALID_ARG;
     auto it = c->plans.find(plan_id);
     if (it == c->plans.end()) return GPUMCD_ERR_NOT_FOUND;
+    if (it->second.inflight > 0) return GPUMCD_ERR_STATE;
     ST(set_device(c));
     cudaStreamSynchronize(c->stream);
     dev_free(c, it->second.tally);
@@ -475,13 +527,16 @@ gpumcd_status gpumcd_plan_reset(gpumcd_ctx *c, int32_t plan_id, uint64_t seed, v
     if (!c) return GPUMCD_ERR_INVALID_ARG;
     auto it = c->plans.find(plan_id);
     if (it == c->plans.end()) return GPUMCD_ERR_NOT_FOUND;
+    if (it->second.inflight > 0) return GPUMCD_ERR_STATE;
     ST(set_device(c));
     cudaStream_t s = pick(c, stream);
     Plan &p = it->second;
     CK(cudaMemsetAsync(p.tally.p, 0, p.tally.bytes, s));
     CK(cudaMemsetAsync(p.ledger.p, 0, p.ledger.bytes, s));
     p.seed = seed;
+    p.hist_sub = 0;
     p.hist_done = 0;
+    p.failed = false;
     p.acc = gpumcd_run_stats{};
     return GPUMCD_OK;
 }
@@ -494,8 +549,80 @@ gpumcd_status gpumcd_plan_histories(gpumcd_ctx *c, int32_t plan_id, uint64_t *h)
     return GPUMCD_OK;
 }
 
-gpumcd_status gpumcd_run(gpumcd_ctx *c, int32_t n_plans, const int32_t *ids, const uint64_t *n_hist, void *stream) {
-    if (!c || n_plans < 1 || n_plans > GPUMCD_MAX_PLANS_PER_RUN || !ids || !n_hist) return GPUMCD_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+// Enqueue launch k of a sequence: the in-queue is the previous launch's
+// out-queue (empty for k = 0), both cursors restart at 0.
+gpumcd_status launch_one(gpumcd_ctx *c, Slot &sl) {
+    const int bi = (int)(sl.k & 1u), bo = bi ^ 1;
+    Control *dc = (Control *)sl.control.p;
+    TransportArgs &A = sl.A;
+    for (int t = 0; t < NT; ++t) {
+        A.in[t].rec = (Rec *)sl.queue[bi][t].p;
+        A.in[t].cursor = &dc->qcur[bi][t];
+        A.in[t].capacity = c->launch.overflow_capacity;
+        A.out[t].rec = (Rec *)sl.queue[bo][t].p;
+        A.out[t].cursor = &dc->qcur[bo][t];
+        A.out[t].capacity = c->launch.overflow_capacity;
+        A.in_count[t] = sl.in_count[t];
+    }
+    CK(cudaMemsetAsync(dc->qcur, 0, sizeof(dc->qcur), sl.s));
+    CK(launch_transport(A, sl.grid, sl.block, sl.bps, sl.s));
+    CK(cudaMemcpyAsync(sl.h_control, dc, sizeof(Control), cudaMemcpyDeviceToHost, sl.s));
+    CK(cudaEventRecord(sl.done, sl.s));
+    ++sl.k;
+    return GPUMCD_OK;
+}
+
+// Settle a sequence: per-plan accounting, then the slot is free again.
+void seq_close(gpumcd_ctx *c, Slot &sl, gpumcd_status result, float ms) {
+    for (size_t i = 0; i < sl.ids.size(); ++i) {
+        auto it = c->plans.find(sl.ids[i]);
+        if (it == c->plans.end()) continue;
+        Plan &p = it->second;
+        --p.inflight;
+        if (result == GPUMCD_OK) p.hist_done += sl.n_hist[i];
+        else p.failed = true;
+        p.acc.n_launches += sl.k;
+        p.acc.transport_ms += ms;
+    }
+    if (result == GPUMCD_OK || sl.k > 0) {
+        c->last = *sl.h_control;
+        c->have_last = true;
+        // run-wide counters go to every plan of a single-plan run and to the first plan otherwise
+        auto it = c->plans.find(sl.ids[0]);
+        if (it != c->plans.end()) {
+            gpumcd_run_stats &a = it->second.acc;
+            const unsigned long long *n = c->last.counters;
+            a.n_photon_events += n[CNT_PH_EVENTS];
+            a.n_photon_real += n[CNT_PH_REAL];
+            a.n_compton += n[CNT_COMPTON];
+            a.n_photo += n[CNT_PHOTO];
+            a.n_pair += n[CNT_PAIR];
+            a.n_electron_steps += n[CNT_E_STEPS];
+            a.n_hard_real += n[CNT_HARD_REAL];
+            a.n_hard_fict += n[CNT_HARD_FICT];
+            a.n_moller += n[CNT_MOLLER];
+            a.n_brem += n[CNT_BREM];
+            a.n_photons += n[CNT_PHOTONS];
+            a.n_electrons += n[CNT_ELECTRONS];
+            a.n_overflow += n[CNT_OVERFLOW];
+            a.n_spilled += n[CNT_SPILLS];
+            a.n_sampler_capped += n[CNT_SAMPLER_CAP];
+        }
+    }
+    sl.busy = false;
+    sl.ticket = 0;
+    sl.ids.clear();
+    sl.n_hist.clear();
+}
+
+// Validate a run request and enqueue its first launch on stream s.
+gpumcd_status seq_start(gpumcd_ctx *c, Slot &sl, int32_t n_plans, const int32_t *ids, const uint64_t *n_hist,
+                        cudaStream_t s) {
+    if (n_plans < 1 || n_plans > GPUMCD_MAX_PLANS_PER_RUN || !ids || !n_hist) return GPUMCD_ERR_INVALID_ARG;
     if (!c->tables) return GPUMCD_ERR_STATE;
     std::vector<Plan *> pl(n_plans);
     for (int i = 0; i < n_plans; ++i) {
@@ -504,21 +631,21 @@ gpumcd_status gpumcd_run(gpumcd_ctx *c, int32_t n_plans, const int32_t *ids, con
         for (int j = 0; j < i; ++j)
             if (ids[j] == ids[i]) return GPUMCD_ERR_INVALID_ARG;
         pl[i] = &it->second;
-        if (pl[i]->hist_done + n_hist[i] > (1ull << 32)) return GPUMCD_ERR_INVALID_ARG;
+        if (pl[i]->failed) return GPUMCD_ERR_STATE;
+        if (pl[i]->hist_sub + n_hist[i] > (1ull << 32)) return GPUMCD_ERR_INVALID_ARG;
     }
     ST(set_device(c));
-    cudaStream_t s = pick(c, stream);
-    const int block = (int)c->launch.block_threads;
-    const int grid = c->n_sm * (int)c->launch.blocks_per_sm;
-    ST(ensure_scratch(c, grid, block));
+    sl.block = (int)c->launch.block_threads;
+    sl.bps = (int)c->launch.blocks_per_sm;
+    sl.grid = c->n_sm * sl.bps;
+    ST(ensure_slot(c, sl, sl.grid, sl.block));
 
-    std::vector<PlanDev> pd(n_plans);
-    TransportArgs A;
+    TransportArgs &A = sl.A;
     memset(&A, 0, sizeof A);
     for (int i = 0; i < n_plans; ++i) {
         const Plan &p = *pl[i];
         const Phantom &ph = c->phantoms.at(p.phantom);
-        PlanDev &d = pd[i];
+        PlanDev &d = sl.h_plandev[i];
         memset(&d, 0, sizeof d);
         d.vox = (const uint32_t *)ph.vox.p;
         d.tally = (unsigned long long *)p.tally.p;
@@ -548,20 +675,20 @@ gpumcd_status gpumcd_run(gpumcd_ctx *c, int32_t n_plans, const int32_t *ids, con
         d.src_type = p.particle;
         d.beam = p.beam;
         d.e_src_q = (uint32_t)std::llround(p.energy / kQ);
-        d.hist_base = p.hist_done;
+        d.hist_base = p.hist_sub;
         d.n_hist = n_hist[i];
         const int t = p.particle;
         A.prim_plan[t][A.n_prim_plans[t]] = (uint8_t)i;
         A.prim_off[t][A.n_prim_plans[t] + 1] = A.prim_off[t][A.n_prim_plans[t]] + n_hist[i];
         A.n_prim_plans[t]++;
     }
-    Control *dc = (Control *)c->control.p;
+    Control *dc = (Control *)sl.control.p;
     A.tables = (const float *)c->tab.p;
     A.phys = c->dphys;
-    A.plans = (const PlanDev *)c->plandev.p;
+    A.plans = (const PlanDev *)sl.plandev.p;
     A.n_plans = n_plans;
     A.prim_cursor = dc->prim_cursor;
-    A.stacks = (Rec *)c->stacks.p;
+    A.stacks = (Rec *)sl.stacks.p;
     A.stack_cap = c->launch.stack_capacity;
     A.switch_high = c->launch.switch_high;
     A.refill_low = c->launch.refill_low;
@@ -570,72 +697,131 @@ gpumcd_status gpumcd_run(gpumcd_ctx *c, int32_t n_plans, const int32_t *ids, con
     A.counters = dc->counters;
     A.error = &dc->error;
 
-    CK(cudaMemcpyAsync(c->plandev.p, pd.data(), sizeof(PlanDev) * n_plans, cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(dc, 0, sizeof(Control), s));
-    CK(cudaEventRecord(c->ev0, s));
+    sl.s = s;
+    sl.k = 0;
+    sl.in_count[0] = sl.in_count[1] = 0;
+    sl.ids.assign(ids, ids + n_plans);
+    sl.n_hist.assign(n_hist, n_hist + n_plans);
+    sl.busy = true;
+    for (int i = 0; i < n_plans; ++i) {
+        pl[i]->hist_sub += n_hist[i];
+        ++pl[i]->inflight;
+    }
+    gpumcd_status st = GPUMCD_OK;
+    cudaError_t e = cudaMemcpyAsync(sl.plandev.p, sl.h_plandev, sizeof(PlanDev) * n_plans, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dc, 0, sizeof(Control), s);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.ev0, s);
+    st = cuda_status(e);
+    if (st == GPUMCD_OK) st = launch_one(c, sl);
+    if (st != GPUMCD_OK) {
+        if (sl.s) cudaStreamSynchronize(sl.s);
+        seq_close(c, sl, st, 0.f);
+    }
+    return st;
+}
+
+// Wait for the sequence's last enqueued launch; relaunch over the overflow
+// queues while they hold particles; then account and free the slot.
+gpumcd_status seq_finish(gpumcd_ctx *c, Slot &sl) {
     gpumcd_status result = GPUMCD_OK;
-    uint32_t launches = 0;
-    unsigned long long in_count[NT] = {0, 0};
-    for (int k = 0; k < 1000; ++k) {
-        const int bi = k & 1, bo = bi ^ 1;
-        for (int t = 0; t < NT; ++t) {
-            A.in[t].rec = (Rec *)c->queue[bi][t].p;
-            A.in[t].cursor = &dc->qcur[bi][t];
-            A.in[t].capacity = c->launch.overflow_capacity;
-            A.out[t].rec = (Rec *)c->queue[bo][t].p;
-            A.out[t].cursor = &dc->qcur[bo][t];
-            A.out[t].capacity = c->launch.overflow_capacity;
-            A.in_count[t] = in_count[t];
-        }
-        CK(cudaMemsetAsync(dc->qcur[bo], 0, sizeof(dc->qcur[bo]), s));
-        CK(launch_transport(A, grid, block, (int)c->launch.blocks_per_sm, s));
-        ++launches;
-        CK(cudaMemcpyAsync(c->h_control, dc, sizeof(Control), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        if (c->h_control->error != 0) {
-            result = c->h_control->error;
+    for (;;) {
+        cudaError_t e = cudaEventSynchronize(sl.done);
+        if (e != cudaSuccess) {
+            result = cuda_status(e);
             break;
         }
+        const Control &hc = *sl.h_control;
+        if (hc.error != 0) {
+            result = hc.error;
+            break;
+        }
+        const int bo = (int)((sl.k - 1u) & 1u) ^ 1;
         bool more = false;
         for (int t = 0; t < NT; ++t) {
-            const unsigned long long o = c->h_control->qcur[bo][t];
-            in_count[t] = o < c->launch.overflow_capacity ? o : c->launch.overflow_capacity;
+            const unsigned long long o = hc.qcur[bo][t];
+            sl.in_count[t] = o < c->launch.overflow_capacity ? o : c->launch.overflow_capacity;
             more = more || o > 0;
         }
         if (!more) break;
-        // this launch's output becomes the next launch's input: restart its cursor
-        CK(cudaMemsetAsync(dc->qcur[bo], 0, sizeof(dc->qcur[bo]), s));
-        if (k == 999) result = GPUMCD_ERR_TIMEOUT;
+        if (sl.k >= 1000) {
+            result = GPUMCD_ERR_TIMEOUT;
+            break;
+        }
+        result = launch_one(c, sl);
+        if (result != GPUMCD_OK) break;
     }
-    CK(cudaEventRecord(c->ev1, s));
-    CK(cudaEventSynchronize(c->ev1));
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-    const Control &hc = *c->h_control;
-    for (int i = 0; i < n_plans; ++i) {
-        Plan &p = *pl[i];
-        if (result == GPUMCD_OK) p.hist_done += n_hist[i];
-        p.acc.n_launches += launches;
-        p.acc.transport_ms += ms;
-    }
-    // run-wide counters go to every plan of a single-plan run and to the first plan otherwise
-    Plan &p0 = *pl[0];
-    p0.acc.n_photon_events += hc.counters[CNT_PH_EVENTS];
-    p0.acc.n_photon_real += hc.counters[CNT_PH_REAL];
-    p0.acc.n_compton += hc.counters[CNT_COMPTON];
-    p0.acc.n_photo += hc.counters[CNT_PHOTO];
-    p0.acc.n_pair += hc.counters[CNT_PAIR];
-    p0.acc.n_electron_steps += hc.counters[CNT_E_STEPS];
-    p0.acc.n_hard_real += hc.counters[CNT_HARD_REAL];
-    p0.acc.n_hard_fict += hc.counters[CNT_HARD_FICT];
-    p0.acc.n_moller += hc.counters[CNT_MOLLER];
-    p0.acc.n_brem += hc.counters[CNT_BREM];
-    p0.acc.n_photons += hc.counters[CNT_PHOTONS];
-    p0.acc.n_electrons += hc.counters[CNT_ELECTRONS];
-    p0.acc.n_overflow += hc.counters[CNT_OVERFLOW];
-    p0.acc.n_spilled += hc.counters[CNT_SPILLS];
-    p0.acc.n_sampler_capped += hc.counters[CNT_SAMPLER_CAP];
+    if (cudaEventRecord(sl.ev1, sl.s) == cudaSuccess && cudaEventSynchronize(sl.ev1) == cudaSuccess)
+        cudaEventElapsedTime(&ms, sl.ev0, sl.ev1);
+    else
+        cudaGetLastError();
+    seq_close(c, sl, result, ms);
     return result;
+}
+
+Slot *find_ticket(gpumcd_ctx *c, int32_t ticket) {
+    for (int i = 1; i <= GPUMCD_MAX_INFLIGHT; ++i)
+        if (c->slot[i].busy && c->slot[i].ticket == ticket) return &c->slot[i];
+    return nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+gpumcd_status gpumcd_run(gpumcd_ctx *c, int32_t n_plans, const int32_t *ids, const uint64_t *n_hist, void *stream) {
+    if (!c) return GPUMCD_ERR_INVALID_ARG;
+    Slot &sl = c->slot[0];
+    if (sl.busy) return GPUMCD_ERR_STATE;
+    ST(seq_start(c, sl, n_plans, ids, n_hist, pick(c, stream)));
+    return seq_finish(c, sl);
+}
+
+gpumcd_status gpumcd_submit(gpumcd_ctx *c, int32_t n_plans, const int32_t *ids, const uint64_t *n_hist,
+                            int32_t *ticket) {
+    if (!c || !ticket) return GPUMCD_ERR_INVALID_ARG;
+    *ticket = 0;
+    Slot *sl = nullptr;
+    for (int i = 1; i <= GPUMCD_MAX_INFLIGHT && !sl; ++i)
+        if (!c->slot[i].busy) sl = &c->slot[i];
+    if (!sl) return GPUMCD_ERR_STATE;
+    ST(set_device(c));
+    if (!sl->own) {
+        int least = 0, greatest = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        CK(cudaStreamCreateWithPriority(&sl->own, cudaStreamNonBlocking, least));
+    }
+    // after everything already enqueued on the context stream (plan resets, phantoms)
+    CK(cudaEventRecord(c->order, c->stream));
+    CK(cudaStreamWaitEvent(sl->own, c->order, 0));
+    ST(seq_start(c, *sl, n_plans, ids, n_hist, sl->own));
+    sl->ticket = c->next_ticket++;
+    if (c->next_ticket <= 0) c->next_ticket = 1;
+    *ticket = sl->ticket;
+    return GPUMCD_OK;
+}
+
+gpumcd_status gpumcd_poll(gpumcd_ctx *c, int32_t ticket, int32_t *done) {
+    if (!c || !done) return GPUMCD_ERR_INVALID_ARG;
+    *done = 0;
+    Slot *sl = find_ticket(c, ticket);
+    if (!sl) return GPUMCD_ERR_NOT_FOUND;
+    ST(set_device(c));
+    const cudaError_t e = cudaEventQuery(sl->done);
+    if (e == cudaErrorNotReady) {
+        cudaGetLastError();
+        return GPUMCD_OK;
+    }
+    *done = 1;
+    return seq_finish(c, *sl);
+}
+
+gpumcd_status gpumcd_wait(gpumcd_ctx *c, int32_t ticket) {
+    if (!c) return GPUMCD_ERR_INVALID_ARG;
+    Slot *sl = find_ticket(c, ticket);
+    if (!sl) return GPUMCD_ERR_NOT_FOUND;
+    ST(set_device(c));
+    return seq_finish(c, *sl);
 }
 
 gpumcd_status gpumcd_plan_result(gpumcd_ctx *c, int32_t plan_id, double thr, double *dose, double *sigma,
@@ -644,6 +830,7 @@ gpumcd_status gpumcd_plan_result(gpumcd_ctx *c, int32_t plan_id, double thr, dou
     auto it = c->plans.find(plan_id);
     if (it == c->plans.end()) return GPUMCD_ERR_NOT_FOUND;
     if (!(thr >= 0.0 && thr <= 1.0)) return GPUMCD_ERR_INVALID_ARG;
+    if (it->second.inflight > 0 || it->second.failed) return GPUMCD_ERR_STATE;
     ST(set_device(c));
     cudaStream_t s = pick(c, stream);
     Plan &p = it->second;
@@ -701,6 +888,7 @@ gpumcd_status gpumcd_plan_result_noalloc(gpumcd_ctx *c, int32_t plan_id, double 
     if (it == c->plans.end()) return GPUMCD_ERR_NOT_FOUND;
     if (!(thr >= 0.0 && thr <= 1.0)) return GPUMCD_ERR_INVALID_ARG;
     Plan &p = it->second;
+    if (p.inflight > 0 || p.failed) return GPUMCD_ERR_STATE;
     const Phantom &ph = c->phantoms.at(p.phantom);
     if (ph.nvox > (uint64_t)GPUMCD_NOALLOC_MAX_VOXELS) return GPUMCD_ERR_INVALID_ARG;
     const uint64_t N = p.hist_done;
@@ -791,6 +979,7 @@ gpumcd_status gpumcd_memory(gpumcd_ctx *c, uint64_t *used, uint64_t *budget) {
 
 gpumcd_status gpumcd_set_launch(gpumcd_ctx *c, const gpumcd_launch *l) {
     if (!c || !l) return GPUMCD_ERR_INVALID_ARG;
+    if (any_busy(c)) return GPUMCD_ERR_STATE;
     gpumcd_launch n = c->launch;
     if (l->block_threads) n.block_threads = l->block_threads;
     if (l->blocks_per_sm) n.blocks_per_sm = l->blocks_per_sm;
@@ -889,8 +1078,8 @@ gpumcd_status gpumcd_debug_counters(gpumcd_ctx *c, uint64_t *out, int32_t *count
     if (!c || !count) return GPUMCD_ERR_INVALID_ARG;
     *count = CNT_N;
     if (!out) return GPUMCD_OK;
-    if (!c->h_control) return GPUMCD_ERR_STATE;
-    for (int i = 0; i < CNT_N; ++i) out[i] = c->h_control->counters[i];
+    if (!c->have_last) return GPUMCD_ERR_STATE;
+    for (int i = 0; i < CNT_N; ++i) out[i] = c->last.counters[i];
     return GPUMCD_OK;
 }
 

@@ -2,20 +2,26 @@
 
 Requests (a resident phantom, a beam, a seed) arrive over time.  The server
 admits them as plans while the HBM budget allows, and runs the active plans in
-rounds: each round is one batched persistent launch (gpumcd_run over every
-active plan) in which each plan simulates its next chunk of histories.  After a
-round, each plan's tally is folded (FP64, on the device) and a plan whose
-relative uncertainty s (mean sigma/D over voxels above ``threshold`` x D_max,
-GPUMCD §II.D) has reached ``target`` is retired: its dose is returned and its
-tally memory freed.  New arrivals join at the next round, so work from
-requests that arrived at different times overlaps on the device.
+rounds: each round is one batched persistent launch sequence over the plans
+that still have work before their next fold, each simulating its next chunk
+of histories.  Up to ``MAX_INFLIGHT`` rounds are on the device at once
+(gpumcd_submit), so one round's CTAs fill the SMs that the other round's drain
+frees.  A plan's tally is folded (FP64, on the device) when it reaches the
+history count at which its uncertainty was projected to reach the target and
+none of its histories is in flight; a plan whose relative uncertainty s (mean
+sigma/D over voxels above ``threshold`` x D_max, GPUMCD §II.D) has reached
+``target`` is retired: its dose is returned and its tally memory freed.  New
+arrivals join the next round, so work from requests that arrived at different
+times overlaps on the device.
 
-A plan's histories are numbered from 0 and its random streams depend only on
-(seed, history, lineage, draw), so its result after N histories is the same
-bit for bit whether it ran alone or in any mix, in any chunking.
+A plan's histories are numbered from 0 in submission order and its random
+streams depend only on (seed, history, lineage, draw), so its result after N
+histories is the same bit for bit whether it ran alone or in any mix, in any
+chunking, with any overlap.
 """
 from __future__ import annotations
 
+import collections
 import dataclasses
 import heapq
 import math
@@ -24,7 +30,7 @@ from typing import Callable, Dict, List, Optional, Sequence
 
 import numpy as np
 
-from . import Context, GpumcdError, MAX_PLANS_PER_RUN
+from . import Context, GpumcdError, MAX_INFLIGHT, MAX_PLANS_PER_RUN
 
 
 @dataclasses.dataclass
@@ -63,7 +69,9 @@ class _Active:
     plan: int
     admitted_s: float
     bytes: int
-    histories: int = 0
+    histories: int = 0   # histories of finished rounds
+    submitted: int = 0   # histories handed to rounds (finished or in flight)
+    inflight: int = 0    # rounds in flight that include the plan
     s_thr: float = float("inf")
     rounds: int = 0
     next_check: int = 0  # history count at which the tally is next folded
@@ -102,6 +110,7 @@ class Server:
         self.max_active = 0
         self.max_used = 0
         self.folds = 0
+        self.inflight: collections.deque = collections.deque()  # (ticket, [(plan, histories)])
         self.t0 = None
 
     # ---- requests ------------------------------------------------------
@@ -142,28 +151,47 @@ class Server:
         """Histories for a plan's next round: its first chunk, then up to the
         point where its tally is next folded, within its share of the round."""
         q = self._quantum()
-        if a.histories == 0:
-            n = self.first_chunk
+        if a.submitted == 0:
             a.next_check = self.first_chunk
-        else:
-            n = min(a.next_check - a.histories, share)
+        n = min(a.next_check - a.submitted, share)
         n = max(q, -(-n // q) * q)
-        return int(max(1, min(n, a.req.max_histories - a.histories)))
+        return int(max(1, min(n, a.req.max_histories - a.submitted)))
 
-    def _round(self) -> None:
-        plans = list(self.active.values())
-        share = max(self.round_histories // max(len(plans), 1), self._quantum())
-        chunks = [self._chunk(a, share) for a in plans]
-        self.ctx.run([a.plan for a in plans], chunks)
-        self.rounds += 1
-        for a, n in zip(plans, chunks):
+    def _runnable(self) -> List[_Active]:
+        return [a for a in self.active.values()
+                if a.submitted < max(a.next_check, 1) and a.submitted < a.req.max_histories]
+
+    def _submit_rounds(self) -> None:
+        """Fill the free launch slots with rounds over the plans that have work."""
+        while len(self.inflight) < MAX_INFLIGHT:
+            plans = self._runnable()
+            if not plans:
+                return
+            share = max(self.round_histories // len(plans), self._quantum())
+            chunks = [self._chunk(a, share) for a in plans]
+            ticket = self.ctx.submit([a.plan for a in plans], chunks)
+            for a, n in zip(plans, chunks):
+                a.submitted += n
+                a.inflight += 1
+            self.inflight.append((ticket, list(zip(plans, chunks))))
+            self.rounds += 1
+
+    def _finish_oldest(self) -> None:
+        ticket, pairs = self.inflight.popleft()
+        self.ctx.wait(ticket)
+        for a, n in pairs:
             a.histories += n
+            a.inflight -= 1
             a.rounds += 1
             self.total_histories += n
-        now = self._now()
-        for a in plans:
+
+    def _fold_ready(self) -> None:
+        """Fold every plan at its checkpoint with no histories in flight."""
+        for a in list(self.active.values()):
+            if a.inflight or a.submitted == 0:
+                continue
             if a.histories < a.next_check and a.histories < a.req.max_histories:
-                continue  # not yet at its projected history count: no fold this round
+                continue
             self.folds += 1
             if self.keep_dose:
                 import torch
@@ -174,8 +202,8 @@ class Server:
                 st = self.ctx.plan_result(a.plan, self.threshold)
             a.s_thr = st["s_thr"] if st["s_thr"] > 0 else float("inf")
             if a.s_thr <= self.target or a.histories >= a.req.max_histories:
-                res = DoseResult(a.req.rid, a.histories, a.s_thr, a.req.arrival_s, a.admitted_s, now,
-                                 a.rounds)
+                res = DoseResult(a.req.rid, a.histories, a.s_thr, a.req.arrival_s, a.admitted_s,
+                                 self._now(), a.rounds)
                 if self.keep_dose:
                     res.dose, res.sigma = d.cpu().numpy(), s.cpu().numpy()
                 self.results.append(res)
@@ -192,18 +220,36 @@ class Server:
         """Serves every submitted request.  With real_time, requests become
         visible at their arrival times on the server clock; otherwise all at once."""
         self.t0 = self.clock()
+        self.inflight = collections.deque()
         if not real_time:
             self.waiting = [(0.0, r, q) for (_, r, q) in self.waiting]
             heapq.heapify(self.waiting)
-        while self.waiting or self.active:
-            self._admit()
-            if not self.active:
-                if self.waiting:
-                    dt = self.waiting[0][0] - self._now()
-                    if dt > 0:
-                        time.sleep(min(dt, 0.05))
-                continue
-            self._round()
+        try:
+            while self.waiting or self.active or self.inflight:
+                self._admit()
+                self._submit_rounds()
+                if not self.inflight:
+                    before = len(self.active)
+                    self._fold_ready()
+                    if self.active and len(self.active) == before and not self._runnable():
+                        raise RuntimeError("served plans stalled")  # cannot happen: folds move next_check
+                    if not self.active and self.waiting:
+                        dt = self.waiting[0][0] - self._now()
+                        if dt > 0:
+                            time.sleep(min(dt, 0.05))
+                    continue
+                self._finish_oldest()
+                # keep the device busy before blocking on folds
+                self._admit()
+                self._submit_rounds()
+                self._fold_ready()
+        finally:
+            while self.inflight:  # leave no sequence in flight on an error
+                ticket, _ = self.inflight.popleft()
+                try:
+                    self.ctx.wait(ticket)
+                except GpumcdError:
+                    pass
         return self.results
 
     # ---- reporting ----------------------------------------------------------

@@ -51,3 +51,17 @@ def test_init_without_gpu_reports_cuda_error():
     assert g.lib().gpumcd_init(ctypes.byref(h), 0, 0) == g.ERR_CUDA
     assert not h.value
     assert g.lib().gpumcd_destroy(None) == g.OK
+
+
+def test_binding_constants_match_the_header():
+    text = open(HEADER).read()
+    defs = {k: int(v) for k, v in re.findall(r"^#define (GPUMCD_\w+) \(?(-?\d+)u?\)?", text, flags=re.M)}
+    assert defs["GPUMCD_MAX_PLANS_PER_RUN"] == g.MAX_PLANS_PER_RUN
+    assert defs["GPUMCD_MAX_INFLIGHT"] == g.MAX_INFLIGHT
+    for name, value in (("OK", g.OK), ("ERR_INVALID_ARG", g.ERR_INVALID_ARG), ("ERR_OOM", g.ERR_OOM),
+                        ("ERR_CUDA", g.ERR_CUDA), ("ERR_QUEUE_OVERFLOW", g.ERR_QUEUE_OVERFLOW),
+                        ("ERR_TIMEOUT", g.ERR_TIMEOUT), ("ERR_NOT_FOUND", g.ERR_NOT_FOUND),
+                        ("ERR_BUDGET", g.ERR_BUDGET), ("ERR_STATE", g.ERR_STATE),
+                        ("ERR_CORRUPT", g.ERR_CORRUPT)):
+        assert defs["GPUMCD_" + name] == value, name
+        assert g.status_string(value) == g.STATUS[value]

@@ -113,3 +113,64 @@ def test_server_admits_within_budget():
     with pytest.raises(g.GpumcdError):
         tiny.submit(DoseRequest(9, pids[0], phantoms[0].nvox, srcs[0], 1, 0.0))
     ctx.close()
+
+
+def test_overlapping_submitted_sequences_equal_one_run():
+    """One plan in two sequences in flight at once (and other plans beside it)
+    ends with the tally of a single synchronous run of the same histories."""
+    ctx = make_ctx()
+    specs = _specs(4, seed=48)
+    phantoms, pids, srcs = _setup(ctx, specs)
+    a = [ctx.plan_open(pid, src, sp.seed, 16) for pid, src, sp in zip(pids, srcs, specs)]
+    t1 = ctx.submit([a[0], a[1]], [32_000, 16_000])
+    t2 = ctx.submit([a[0], a[2], a[3]], [48_000, 16_000, 16_000])
+    with pytest.raises(g.GpumcdError) as e:
+        ctx.submit([a[3]], [16])  # both slots busy
+    assert e.value.status == g.ERR_STATE
+    with pytest.raises(g.GpumcdError) as e:
+        ctx.plan_result(a[0], 0.5)  # in flight
+    assert e.value.status == g.ERR_STATE
+    with pytest.raises(g.GpumcdError) as e:
+        ctx.plan_close(a[2])
+    assert e.value.status == g.ERR_STATE
+    while not ctx.poll(t2):
+        pass
+    ctx.wait(t1)
+    with pytest.raises(g.GpumcdError) as e:
+        ctx.wait(t1)  # already finished
+    assert e.value.status == g.ERR_NOT_FOUND
+    assert ctx.plan_histories(a[0]) == 80_000
+    for i, n in ((0, 80_000), (1, 16_000), (2, 16_000), (3, 16_000)):
+        b = ctx.plan_open(pids[i], srcs[i], specs[i].seed, 16)
+        ctx.run([b], [n])
+        x = _dose(ctx, a[i], phantoms[i].nvox)
+        y = _dose(ctx, b, phantoms[i].nvox)
+        assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+        assert x[2]["e_deposited"] + x[2]["e_escaped"] + x[2]["e_rest"] == x[2]["e_incident"]
+        assert x[2]["e_incident"] == y[2]["e_incident"]
+        ctx.plan_close(b)
+    ctx.close()
+
+
+def test_failed_sequence_marks_its_plans():
+    """A submitted sequence that overflows its queue reports the error at
+    wait, and its plan returns ERR_STATE until it is reset."""
+    ctx = make_ctx(overflow_capacity=64, block_threads=64, blocks_per_sm=1, stack_capacity=128,
+                   switch_high=128)
+    ph = W.z_slabs((24, 20, 32), 0.5, [(3.0, W.MAT_WATER, 1.0), (2.0, W.MAT_BONE, 1.85),
+                                        (4.0, W.MAT_LUNG, 0.26), (1e9, W.MAT_WATER, 1.0)])
+    pid = ctx.create_phantom(ph)
+    src = W.Source(W.PHOTON, W.BEAM_SQUARE, energy=15.0, center_cm=(6.0, 5.0), field_cm=4.0)
+    p = ctx.plan_open(pid, src, 5, 16)
+    t = ctx.submit([p], [200_000])
+    with pytest.raises(g.GpumcdError) as e:
+        ctx.wait(t)
+    assert e.value.status == g.ERR_QUEUE_OVERFLOW
+    with pytest.raises(g.GpumcdError) as e:
+        ctx.plan_result(p, 0.5)
+    assert e.value.status == g.ERR_STATE
+    ctx.plan_reset(p, 5)
+    ctx.set_launch(overflow_capacity=1 << 20)
+    ctx.run([p], [1_600])
+    assert ctx.plan_result(p, 0.5)["histories"] == 1_600
+    ctx.close()
