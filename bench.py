@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--workload", default="c2", choices=["c2", "batched", "served"],
                     help="c2: the contract line; batched: 64 uneven plans in one launch vs alone; "
                          "served: a Poisson request stream with continuous batching")
+    ap.add_argument("--graph", action="store_true",
+                    help="launch each sequence's first launch from a captured CUDA graph")
     ap.add_argument("--requests", type=int, default=1000, help="served: number of requests")
     ap.add_argument("--calibration", type=int, default=48,
                     help="served: requests of the capacity run (served vs alone)")
@@ -204,6 +206,8 @@ def run_ours(args):
     pe, pg = W.config2(W.ELECTRON), W.config2(W.PHOTON)
     nvox = pe.phantom.nvox
     ctx = g.engine(local)
+    if args.graph:
+        ctx.set_launch(flags=g.LAUNCH_GRAPH)
     stream = torch.cuda.Stream(device=dev)
     sh = stream.cuda_stream
     pid = ctx.create_phantom(pe.phantom)
@@ -278,6 +282,7 @@ def run_ours(args):
                        "phantom": "128^3 water, 0.25 cm", "beams": "15 MeV 10x10 cm^2 e- 1e6, photons 4e6",
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "launch_graph": bool(args.graph),
                        "s05_electron": st_e["s_thr"], "s05_photon": st_g["s_thr"],
                        "transport_ms_electron": st_e["transport_ms"],
                        "transport_ms_photon": st_g["transport_ms"],
@@ -324,6 +329,8 @@ def run_batched(args):
     specs = W.config4()
     phantoms = c4_phantoms(specs)
     ctx = g.engine(0)
+    if args.graph:
+        ctx.set_launch(flags=g.LAUNCH_GRAPH)
     pids = [ctx.create_phantom(ph) for ph in phantoms]
     srcs = [W.square_field(sp.particle, sp.energy, ph, sp.field_cm) for sp, ph in zip(specs, phantoms)]
     nh = [-(-sp.n_histories // 16) * 16 for sp in specs]  # whole multiples of the 16 batches
@@ -376,7 +383,7 @@ def run_batched(args):
           "electron_plans": int(sum(sp.particle for sp in specs)),
           "ledger_exact": all(x["e_deposited"] + x["e_escaped"] + x["e_rest"] == x["e_incident"] for x in st),
           "autotuned_launch": tuned["launch"], "autotune_trials": len(tuned["trials"]),
-          "n_batches": 16, "steps": args.steps, "data": "synthetic"})
+          "n_batches": 16, "steps": args.steps, "launch_graph": bool(args.graph), "data": "synthetic"})
     ctx.close()
 
 
@@ -395,6 +402,8 @@ def run_served(args):
     phantoms = c4_phantoms(pool_specs)
     budget = int(args.budget_gb * 2 ** 30)
     ctx = g.engine(0, hbm_budget_bytes=budget + (8 << 30))
+    if args.graph:
+        ctx.set_launch(flags=g.LAUNCH_GRAPH)
     pids = [ctx.create_phantom(ph) for ph in phantoms]
 
     def requests(rate):
@@ -439,6 +448,7 @@ def run_served(args):
           "latency_p99_s": rep["latency_p99_s"], "wall_s": rep["wall_s"], "rounds": rep["rounds"],
           "folds": rep["folds"], "mean_histories_per_request": rep["histories"] / max(rep["requests"], 1),
           "s_thr_max": rep["s_thr_max"], "rounds_in_flight": g.MAX_INFLIGHT, "hbm_budget_gb": args.budget_gb,
+          "launch_graph": bool(args.graph),
           "phantoms": "64 resident config-4 phantoms, request i on phantom i mod 64", "data": "synthetic"})
     ctx.close()
 

@@ -97,7 +97,7 @@ typedef struct {
 
 /* Launch tuning; 0 in a field keeps the current value.  See gpumcd_set_launch. */
 typedef struct {
-    uint32_t block_threads;   /* threads per CTA (multiple of 32, <= 1024) */
+    uint32_t block_threads;   /* threads per CTA (multiple of 32, <= 512) */
     uint32_t blocks_per_sm;   /* resident CTAs per SM of the persistent grid */
     uint32_t stack_capacity;  /* per-warp particle stack entries per type */
     uint32_t switch_high;     /* a warp switches type when the other stack holds this many (= stack_capacity: never) */
@@ -109,6 +109,7 @@ typedef struct {
 
 #define GPUMCD_LAUNCH_WARP_AGGREGATE 1u /* combine a warp's deposits to one voxel into one atomic */
 #define GPUMCD_LAUNCH_PROFILE 2u        /* count clock cycles per event type (see gpumcd_debug_counters) */
+#define GPUMCD_LAUNCH_GRAPH 4u          /* replay a sequence's first launch from a captured CUDA graph */
 
 /* Counters of one run.  The ledger satisfies, exactly,
  * e_deposited + e_escaped + e_rest == e_incident. */

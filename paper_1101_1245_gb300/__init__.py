@@ -28,6 +28,7 @@ PHOTON, ELECTRON = 0, 1
 BEAM_PENCIL, BEAM_SQUARE = 0, 1
 LAUNCH_WARP_AGGREGATE = 1
 LAUNCH_PROFILE = 2
+LAUNCH_GRAPH = 4
 PARTICLE_TYPES = ("photon", "electron")
 
 STATUS = {

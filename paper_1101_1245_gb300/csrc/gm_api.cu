@@ -73,6 +73,13 @@ struct Slot {
     unsigned long long in_count[NT] = {0, 0};
     std::vector<int32_t> ids;
     std::vector<uint64_t> n_hist;
+    // GPUMCD_LAUNCH_GRAPH: the first launch of a sequence (plan-table copy,
+    // control reset, kernel, control read-back) captured once per launch
+    // shape and replayed with the kernel's arguments updated
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraphNode_t knode = nullptr;
+    int g_grid = 0, g_block = 0, g_bps = 0;
 };
 
 }  // namespace
@@ -209,6 +216,8 @@ void free_slot(gpumcd_ctx *c, Slot &sl) {
     if (sl.ev0) cudaEventDestroy(sl.ev0);
     if (sl.ev1) cudaEventDestroy(sl.ev1);
     if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.gexec) cudaGraphExecDestroy(sl.gexec);
+    if (sl.graph) cudaGraphDestroy(sl.graph);
     if (sl.own) cudaStreamDestroy(sl.own);
     sl = Slot{};
 }
@@ -576,6 +585,78 @@ gpumcd_status launch_one(gpumcd_ctx *c, Slot &sl) {
     return GPUMCD_OK;
 }
 
+// The queue and cursor pointers of launch k = 0 (empty in-queue).
+void first_queues(gpumcd_ctx *c, Slot &sl) {
+    Control *dc = (Control *)sl.control.p;
+    for (int t = 0; t < NT; ++t) {
+        sl.A.in[t].rec = (Rec *)sl.queue[0][t].p;
+        sl.A.in[t].cursor = &dc->qcur[0][t];
+        sl.A.in[t].capacity = c->launch.overflow_capacity;
+        sl.A.out[t].rec = (Rec *)sl.queue[1][t].p;
+        sl.A.out[t].cursor = &dc->qcur[1][t];
+        sl.A.out[t].capacity = c->launch.overflow_capacity;
+        sl.A.in_count[t] = 0;
+    }
+}
+
+// First launch of a sequence from the slot's captured graph.  Its copy and
+// reset nodes touch only slot-owned buffers of fixed size (the whole plan
+// table is copied), so the graph stays valid for the slot's lifetime and
+// only the kernel node's argument block changes between runs; a new launch
+// shape (grid, CTA size, kernel variant) is captured afresh.
+gpumcd_status first_launch_graph(gpumcd_ctx *c, Slot &sl) {
+    first_queues(c, sl);
+    Control *dc = (Control *)sl.control.p;
+    if (!sl.gexec || sl.g_grid != sl.grid || sl.g_block != sl.block || sl.g_bps != sl.bps) {
+        if (sl.gexec) cudaGraphExecDestroy(sl.gexec);
+        if (sl.graph) cudaGraphDestroy(sl.graph);
+        sl.gexec = nullptr;
+        sl.graph = nullptr;
+        sl.knode = nullptr;
+        CK(cudaStreamBeginCapture(sl.s, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaMemcpyAsync(sl.plandev.p, sl.h_plandev, sizeof(PlanDev) * GPUMCD_MAX_PLANS_PER_RUN,
+                                        cudaMemcpyHostToDevice, sl.s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(dc, 0, sizeof(Control), sl.s);
+        if (e == cudaSuccess) e = launch_transport(sl.A, sl.grid, sl.block, sl.bps, sl.s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_control, dc, sizeof(Control), cudaMemcpyDeviceToHost, sl.s);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(sl.s, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&sl.gexec, g, 0);
+        if (e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            sl.gexec = nullptr;
+            return cuda_status(e);
+        }
+        sl.graph = g;
+        size_t n = 0;
+        CK(cudaGraphGetNodes(g, nullptr, &n));
+        std::vector<cudaGraphNode_t> nodes(n);
+        CK(cudaGraphGetNodes(g, nodes.data(), &n));
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType ty;
+            CK(cudaGraphNodeGetType(nd, &ty));
+            if (ty == cudaGraphNodeTypeKernel) sl.knode = nd;
+        }
+        if (!sl.knode) return GPUMCD_ERR_CUDA;
+        sl.g_grid = sl.grid;
+        sl.g_block = sl.block;
+        sl.g_bps = sl.bps;
+    } else {
+        cudaKernelNodeParams kp;
+        CK(cudaGraphKernelNodeGetParams(sl.knode, &kp));
+        void *args[] = {&sl.A};
+        kp.kernelParams = args;
+        kp.extra = nullptr;
+        CK(cudaGraphExecKernelNodeSetParams(sl.gexec, sl.knode, &kp));
+    }
+    CK(cudaEventRecord(sl.ev0, sl.s));
+    CK(cudaGraphLaunch(sl.gexec, sl.s));
+    CK(cudaEventRecord(sl.done, sl.s));
+    sl.k = 1;
+    return GPUMCD_OK;
+}
+
 // Settle a sequence: per-plan accounting, then the slot is free again.
 void seq_close(gpumcd_ctx *c, Slot &sl, gpumcd_status result, float ms) {
     for (size_t i = 0; i < sl.ids.size(); ++i) {
@@ -708,11 +789,16 @@ gpumcd_status seq_start(gpumcd_ctx *c, Slot &sl, int32_t n_plans, const int32_t 
         ++pl[i]->inflight;
     }
     gpumcd_status st = GPUMCD_OK;
-    cudaError_t e = cudaMemcpyAsync(sl.plandev.p, sl.h_plandev, sizeof(PlanDev) * n_plans, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(dc, 0, sizeof(Control), s);
-    if (e == cudaSuccess) e = cudaEventRecord(sl.ev0, s);
-    st = cuda_status(e);
-    if (st == GPUMCD_OK) st = launch_one(c, sl);
+    if (c->launch.flags & GPUMCD_LAUNCH_GRAPH) {
+        st = first_launch_graph(c, sl);
+    } else {
+        cudaError_t e = cudaMemcpyAsync(sl.plandev.p, sl.h_plandev, sizeof(PlanDev) * n_plans,
+                                        cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(dc, 0, sizeof(Control), s);
+        if (e == cudaSuccess) e = cudaEventRecord(sl.ev0, s);
+        st = cuda_status(e);
+        if (st == GPUMCD_OK) st = launch_one(c, sl);
+    }
     if (st != GPUMCD_OK) {
         if (sl.s) cudaStreamSynchronize(sl.s);
         seq_close(c, sl, st, 0.f);

@@ -1,0 +1,178 @@
+"""FP32 transport (the CUDA path) against the FP64 oracle, per workload: the
+dose-error report for the C1-C3 configurations.  Needs a GPU; run from the
+repository root:
+
+    python tests/report_fp_error.py [--out FILE]
+
+Both sides estimate the same expected dose statistically: the CUDA path at the
+configuration's history count, the oracle at a count its host cores finish in
+about a minute, each as K independent parts.  The compared voxels (dose above
+20% of D_max) and D_max itself come from a third, independent CUDA estimate
+(other seeds).  Selecting on either compared estimate would favour the voxels
+where that estimate fluctuated high and show a spurious difference of its own
+sign.  One JSON object per configuration:
+  mean_abs / max_abs   |D_gpu - D_ora| / D_max
+  noise                the mean combined sigma / D_max that pure noise gives
+  z_mean, z_std        of z = (D_gpu - D_ora) / sigma_combined (meaningful where
+                       the oracle's voxels hold many deposits; "oracle_sparse" is
+                       the fraction of compared voxels with sigma_ora / D_ora > 0.5)
+  pass_3sigma          fraction with |z| <= 3
+  region_bias, _se     relative difference of the region-mean dose, with its
+                       standard error from the spread of the K parts (which
+                       carries the voxel-to-voxel correlation)
+  slabs                for layered phantoms, the same per material layer inside
+                       the central 8 x 8 cm
+  gamma_2_2            2%/2 mm gamma pass rate (C1, C2)
+  dep_frac_gpu/_ora    deposited / incident energy, K-part mean and its standard error
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+K = 8  # independent parts on each side
+CASES = [
+    # name, plan factory, GPU histories, oracle histories, gamma
+    ("c1_water32_2MeV_photon_pencil", "config1", None, 4_000_000, 1_000_000, True),
+    ("c2_water128_15MeV_electron", "config2", "electron", 1_000_000, 200_000, True),
+    ("c2_water128_15MeV_photon", "config2", "photon", 4_000_000, 400_000, True),
+    ("c3_slabs256_6MV_spectrum", "config3", None, 10_000_000, 240_000, False),
+]
+
+
+def _plan(W, factory, particle):
+    if factory == "config2":
+        return W.config2(W.ELECTRON if particle == "electron" else W.PHOTON)
+    return getattr(W, factory)()
+
+
+def gpu_parts(ctx, plan, n_total, seed0=1000):
+    import torch
+    ph = plan.phantom
+    pid = ctx.create_phantom(ph)
+    doses, sigmas, fracs = [], [], []
+    for i in range(K):
+        p = ctx.plan_open(pid, plan.source, seed0 + i, 32)
+        ctx.run([p], [n_total // K])
+        d = torch.zeros(ph.nvox, dtype=torch.float64, device="cuda")
+        s = torch.zeros_like(d)
+        st = ctx.plan_result(p, 0.2, d.data_ptr(), s.data_ptr())
+        doses.append(d.cpu().numpy())
+        sigmas.append(s.cpu().numpy())
+        fracs.append(st["e_deposited"] / st["e_incident"])
+        ctx.plan_close(p)
+    ctx.destroy_phantom(pid)
+    parts = np.array(doses)
+    sigma = np.sqrt(np.sum(np.square(sigmas), axis=0)) / K
+    return parts.mean(0), sigma, np.array(fracs), parts
+
+
+def oracle_parts(plan, n_total, processes):
+    import oracle
+    import workloads as W
+    runs = oracle.simulate_parts(W.MATERIALS, W.DEFAULT_PHYSICS, plan.phantom, plan.source, n_total,
+                                 777, K, processes=processes)
+    n = sum(r.n_histories for r in runs)
+    tot = oracle.OracleResult(n, sum(r.sum_e for r in runs), sum(r.sum_e2 for r in runs), {})
+    fracs = np.array([r.stats["e_deposited"] / r.stats["e_incident"] for r in runs])
+    parts = np.array([r.dose_gy(plan.phantom) for r in runs])
+    return tot.dose_gy(plan.phantom), tot.sigma_gy(plan.phantom), fracs, parts
+
+
+def _ratio(g_m, o_m):
+    ref = o_m.mean()
+    se = np.sqrt(g_m.var(ddof=1) / len(g_m) + o_m.var(ddof=1) / len(o_m)) / ref
+    return float((g_m.mean() - ref) / ref), float(se)
+
+
+def compare(plan, sel, dg, sg, do, so, gamma, g_parts, o_parts):
+    from tests._gamma import gamma_pass_rate
+    dmax = sel.max()
+    m = sel > 0.2 * dmax
+    diff = (dg - do)[m]
+    comb = np.sqrt(sg ** 2 + so ** 2)[m]
+    ok = comb > 0
+    z = diff[ok] / comb[ok]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        sparse = np.mean(~(so[m] <= 0.5 * do[m]))
+    out = {
+        "voxels": int(m.sum()),
+        "mean_abs": float(np.mean(np.abs(diff)) / dmax),
+        "max_abs": float(np.max(np.abs(diff)) / dmax),
+        "noise": float(np.mean(comb) / dmax),
+        "z_mean": float(np.mean(z)),
+        "z_std": float(np.std(z)),
+        "pass_3sigma": float(np.mean(np.abs(z) <= 3.0)),
+        "oracle_sparse": float(sparse),
+    }
+    out["region_bias"], out["region_bias_se"] = _ratio(g_parts[:, m].mean(1), o_parts[:, m].mean(1))
+    ph = plan.phantom
+    nx, ny, nz = ph.dims
+    mats = ph.mat[:, ny // 2, nx // 2]
+    bounds = [0] + [k for k in range(1, nz) if mats[k] != mats[k - 1]] + [nz]
+    if len(bounds) > 2:
+        h = int(round(4.0 / ph.voxel_cm[0]))
+        c = nx // 2
+        slabs = []
+        for z0, z1 in zip(bounds[:-1], bounds[1:]):
+            def mean(d):
+                return d.reshape(-1, nz, ny, nx)[:, z0:z1, c - h:c + h, c - h:c + h].mean(axis=(1, 2, 3))
+            r, se = _ratio(mean(g_parts), mean(o_parts))
+            slabs.append({"z_cm": [round(z0 * ph.voxel_cm[2], 2), round(z1 * ph.voxel_cm[2], 2)],
+                          "material": int(mats[z0]), "bias": r, "bias_se": se})
+        out["slabs"] = slabs
+    if gamma:
+        shape = (nz, ny, nx)
+        vox_mm = tuple(10 * v for v in ph.voxel_cm)
+        out["gamma_2_2"] = gamma_pass_rate(dg.reshape(shape), do.reshape(shape), vox_mm)
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--only", default=None, help="comma-separated case names")
+    args = ap.parse_args()
+    import workloads as W
+    from tests.conftest import host_cores
+    cores = host_cores()
+    cases = [c for c in CASES if not args.only or c[0] in args.only.split(",")]
+    # oracle first: its spawned pool runs before the first GPU call
+    ora = {}
+    for name, factory, particle, n_gpu, n_ora, _ in cases:
+        t0 = time.perf_counter()
+        ora[name] = oracle_parts(_plan(W, factory, particle), n_ora, cores) + (time.perf_counter() - t0,)
+        print(f"oracle {name}: {ora[name][4]:.1f} s", file=sys.stderr, flush=True)
+    import paper_1101_1245_gb300 as g
+    ctx = g.engine(0)
+    lines = []
+    for name, factory, particle, n_gpu, n_ora, gamma in cases:
+        plan = _plan(W, factory, particle)
+        dg, sg, fg, gp = gpu_parts(ctx, plan, n_gpu)
+        sel = gpu_parts(ctx, plan, n_gpu, seed0=5000)[0]  # independent: picks the region and D_max
+        do, so, fo, op, secs = ora[name]
+        rec = {"config": name, "gpu_histories": n_gpu, "oracle_histories": n_ora, "parts": K,
+               "oracle_cores": cores, "oracle_s": round(secs, 1)}
+        rec.update(compare(plan, sel, dg, sg, do, so, gamma, gp, op))
+        rec.update({"dep_frac_gpu": float(fg.mean()), "dep_frac_gpu_se": float(fg.std(ddof=1) / np.sqrt(K)),
+                    "dep_frac_ora": float(fo.mean()), "dep_frac_ora_se": float(fo.std(ddof=1) / np.sqrt(K))})
+        line = json.dumps(rec)
+        print(line, flush=True)
+        lines.append(line)
+    ctx.close()
+    if args.out:
+        with open(args.out, "w") as f:
+            f.write("\n".join(lines) + "\n")
+
+
+if __name__ == "__main__":
+    main()

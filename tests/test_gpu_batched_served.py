@@ -174,3 +174,28 @@ def test_failed_sequence_marks_its_plans():
     ctx.run([p], [1_600])
     assert ctx.plan_result(p, 0.5)["histories"] == 1_600
     ctx.close()
+
+
+def test_graph_launches_equal_direct_launches():
+    """Batched runs of changing plan sets through one slot's captured graph,
+    and submitted sequences through the other slots' graphs, give the tallies
+    of direct launches."""
+    specs = _specs(5, seed=50)
+    out = {}
+    for flags in (0, g.LAUNCH_GRAPH):
+        ctx = make_ctx(flags=flags)
+        phantoms, pids, srcs = _setup(ctx, specs)
+        a = [ctx.plan_open(pid, src, sp.seed, 16) for pid, src, sp in zip(pids, srcs, specs)]
+        ctx.run(a[:3], [16_000, 32_000, 16_000])
+        ctx.run([a[1], a[3], a[4]], [16_000, 48_000, 16_000])
+        t = ctx.submit([a[0], a[4]], [32_000, 16_000])
+        u = ctx.submit([a[2]], [16_000])
+        ctx.wait(u)
+        ctx.wait(t)
+        ctx.run([a[0]], [16_000])
+        out[flags] = [_dose(ctx, p, phantoms[i].nvox) for i, p in enumerate(a)]
+        ctx.close()
+    for x, y in zip(out[0], out[g.LAUNCH_GRAPH]):
+        assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+        assert x[2]["histories"] == y[2]["histories"]
+        assert y[2]["e_deposited"] + y[2]["e_escaped"] + y[2]["e_rest"] == y[2]["e_incident"]

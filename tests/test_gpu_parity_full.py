@@ -138,3 +138,17 @@ def test_c3_full_size_slabs_spectrum(ctx):
     assert three_sigma_pass_rate(dg, sg, do, so, mask) >= 0.99
     rate, n = _curve_parity(_pdd(gd, ph, 1.0), _pdd(od, ph, 1.0))
     assert n > 10 and rate >= 0.97, rate
+    # per slab (water, bone, lung, water): the mean dose inside the central
+    # 8 x 8 cm averages ~1e5 voxels, so it checks the heterogeneity handling
+    # far more sharply than single voxels; the standard errors come from the
+    # spread of the K independent runs on each side
+    nx, ny, nz = ph.dims
+    mats = ph.mat[:, 0, 0]
+    bounds = [0] + [z for z in range(1, nz) if mats[z] != mats[z - 1]] + [nz]
+    c, h = nx // 2, 20
+    for z0, z1 in zip(bounds[:-1], bounds[1:]):
+        def slab(d):
+            return d.reshape(-1, nz, ny, nx)[:, z0:z1, c - h:c + h, c - h:c + h].mean(axis=(1, 2, 3))
+        g_m, o_m = slab(gd), slab(od)
+        se = np.sqrt(g_m.var(ddof=1) / len(g_m) + o_m.var(ddof=1) / len(o_m))
+        assert abs(g_m.mean() - o_m.mean()) <= 3.5 * se, (z0, z1, g_m.mean(), o_m.mean(), se)

@@ -55,6 +55,7 @@ def reference():
          stack_capacity=128),
     dict(flags=g.LAUNCH_WARP_AGGREGATE),
     dict(flags=g.LAUNCH_PROFILE),
+    dict(flags=g.LAUNCH_GRAPH),
     dict(stack_capacity=128, switch_high=64, overflow_capacity=1 << 16, chunk=256),
 ])
 def test_bit_identical_across_launch_shapes(reference, kind, launch):
@@ -72,9 +73,11 @@ def test_bit_identical_across_launch_shapes(reference, kind, launch):
 
 
 @pytest.mark.parametrize("kind", ["electron", "photon"])
-def test_split_runs_equal_one_run(reference, kind):
+@pytest.mark.parametrize("flags", [0, g.LAUNCH_GRAPH])
+def test_split_runs_equal_one_run(reference, kind, flags):
+    """Also replays one captured graph with new kernel arguments per run."""
     ph, out = reference
-    ctx = make_ctx()
+    ctx = make_ctx(flags=flags)
     d, s, st = _dose(ctx, ph, SOURCES[kind], 40_000, 99, splits=(10_000, 17_000, 13_000))
     ctx.close()
     assert np.array_equal(d, out[kind][0])
@@ -87,11 +90,13 @@ SPILL = dict(block_threads=64, blocks_per_sm=1, stack_capacity=128, switch_high=
 
 
 @pytest.mark.parametrize("kind", ["electron", "photon"])
-def test_overflow_path_is_lossless(kind):
-    """Spilled particles finish in further launches with the same result."""
+@pytest.mark.parametrize("flags", [0, g.LAUNCH_GRAPH])
+def test_overflow_path_is_lossless(kind, flags):
+    """Spilled particles finish in further launches with the same result
+    (after a first launch replayed from a graph, too)."""
     ph = _plan()
     n = 200_000 if kind == "photon" else 40_000
-    ctx = make_ctx(overflow_capacity=1 << 20, **SPILL)
+    ctx = make_ctx(overflow_capacity=1 << 20, flags=flags, **SPILL)
     a = _dose(ctx, ph, SOURCES[kind], n, 5)
     ctx.close()
     ctx = make_ctx()
