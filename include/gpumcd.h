@@ -43,7 +43,6 @@ typedef int32_t gpumcd_status;
 #define GPUMCD_ERR_NOT_FOUND (-6)      /* unknown phantom or plan id */
 #define GPUMCD_ERR_BUDGET (-7)         /* the allocation would exceed the context's HBM budget */
 #define GPUMCD_ERR_STATE (-8)          /* a call came in the wrong order (e.g. no materials loaded) */
-#define GPUMCD_ERR_CORRUPT (-9)        /* a kernel found a particle record or voxel word out of range and dropped it */
 
 #define GPUMCD_MAX_MATERIALS 4
 #define GPUMCD_MAX_ELEMENTS 16

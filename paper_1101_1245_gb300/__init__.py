@@ -34,10 +34,10 @@ PARTICLE_TYPES = ("photon", "electron")
 STATUS = {
     0: "ok", -1: "invalid argument", -2: "device out of memory", -3: "CUDA error",
     -4: "particle queue overflow", -5: "device wait timed out", -6: "unknown id",
-    -7: "HBM budget exceeded", -8: "call out of order", -9: "device state check failed",
+    -7: "HBM budget exceeded", -8: "call out of order",
 }
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_QUEUE_OVERFLOW, ERR_TIMEOUT, ERR_NOT_FOUND, \
-    ERR_BUDGET, ERR_STATE, ERR_CORRUPT = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+    ERR_BUDGET, ERR_STATE = 0, -1, -2, -3, -4, -5, -6, -7, -8
 
 
 class GpumcdError(RuntimeError):

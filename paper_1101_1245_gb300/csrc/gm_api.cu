@@ -261,7 +261,6 @@ const char *gpumcd_status_string(gpumcd_status s) {
         case GPUMCD_ERR_NOT_FOUND: return "unknown id";
         case GPUMCD_ERR_BUDGET: return "HBM budget exceeded";
         case GPUMCD_ERR_STATE: return "call out of order";
-        case GPUMCD_ERR_CORRUPT: return "device state check failed";
         default: return "unknown status";
     }
 }
@@ -357,7 +356,6 @@ gpumcd_status gpumcd_load_materials(gpumcd_ctx *c, const gpumcd_material *mats, 
     c->dphys.p_cut_q = (uint32_t)std::llround(ph->p_cut / kQ);
     c->dphys.e_abs_q = (uint32_t)std::llround(ph->e_abs / kQ);
     c->dphys.two_mc2_q = (uint32_t)std::llround(2.0 * kMC2 / kQ);
-    c->dphys.e_max_q = (uint32_t)std::llround(ph->e_max / kQ);
     c->dphys.t_c = (float)ph->t_c;
     c->dphys.k_c = (float)ph->k_c;
     c->dphys.estepe = (float)ph->estepe;
@@ -1086,6 +1084,8 @@ gpumcd_status gpumcd_set_launch(gpumcd_ctx *c, const gpumcd_launch *l) {
     if (n.switch_high < 32 || n.switch_high > n.stack_capacity) return GPUMCD_ERR_INVALID_ARG;
     if (n.refill_low > 32 || n.chunk < 1 || n.chunk > 4096) return GPUMCD_ERR_INVALID_ARG;
     if (n.overflow_capacity < 64 || n.overflow_capacity > (1u << 26)) return GPUMCD_ERR_INVALID_ARG;
+    // the profiling kernel is instantiated for up to 512 threads x 2 CTAs per SM
+    if ((n.flags & GPUMCD_LAUNCH_PROFILE) && n.blocks_per_sm > 2) return GPUMCD_ERR_INVALID_ARG;
     c->launch = n;
     return GPUMCD_OK;
 }

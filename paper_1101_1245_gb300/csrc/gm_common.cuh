@@ -28,6 +28,10 @@ constexpr double kMeVPerGramToGy = 1.602176634e-10;
 constexpr int G = 512;      // points of each energy grid
 constexpr int G_MS = 512;   // points of the multiple-scattering ln(a) table
 constexpr int NMAT = GPUMCD_MAX_MATERIALS;
+// the transport kernel masks a voxel's material id with NMAT - 1
+static_assert((NMAT & (NMAT - 1)) == 0, "NMAT must be a power of two");
+// ...and a record's plan index with GPUMCD_MAX_PLANS_PER_RUN - 1
+static_assert((GPUMCD_MAX_PLANS_PER_RUN & (GPUMCD_MAX_PLANS_PER_RUN - 1)) == 0, "plan table size");
 constexpr double MS_G_MIN = 1e-8;  // paths below this many transport mean free paths: no deflection
 constexpr double MS_G_MAX = 20.0;  // paths above: isotropic
 
@@ -52,7 +56,7 @@ struct Grid {
 
 // Transport parameters in device form.
 struct Phys {
-    uint32_t p_cut_q, e_abs_q, two_mc2_q, e_max_q;
+    uint32_t p_cut_q, e_abs_q, two_mc2_q;
     float t_c, k_c, estepe, nudge;
     Grid grid;
 };

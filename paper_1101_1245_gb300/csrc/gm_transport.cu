@@ -177,22 +177,10 @@ __device__ __forceinline__ void load_rec(Lane &p, const Rec &r) {
     const uint4 c = r.c;
     p.x = a.x; p.y = a.y; p.z = a.z; p.ux = a.w;
     p.uy = b.x; p.uz = b.y; p.E = __float_as_uint(b.z); p.hist = __float_as_uint(b.w);
-    p.lin_lo = c.x; p.lin_hi = c.y; p.draw = c.z; p.plan = c.w;
+    // the plan field indexes the CTA's 64-entry plan table, all of whose
+    // entries are set at launch: masked, it stays in range by construction
+    p.lin_lo = c.x; p.lin_hi = c.y; p.draw = c.z; p.plan = c.w & (GPUMCD_MAX_PLANS_PER_RUN - 1);
     p.act = true;
-}
-
-// A record whose plan index or energy is out of range is dropped and
-// reported (GPUMCD_ERR_CORRUPT) instead of being transported: every later
-// plan and tally access is indexed through the plan field.  (E may be 0: an
-// electron whose whole energy went to a bremsstrahlung photon; E may exceed
-// e_max by the FP32 rounding of a spectrum's top edge, hence the margin.)
-__device__ __forceinline__ void load_checked(const TransportArgs &A, Lane &p, const Rec &r) {
-    load_rec(p, r);
-    if (p.plan >= (uint32_t)A.n_plans || p.E > A.phys.e_max_q + (A.phys.e_max_q >> 8)) {
-        atomicExch(A.error, GPUMCD_ERR_CORRUPT);
-        p.act = false;
-        p.plan = 0u;
-    }
 }
 
 __device__ __forceinline__ Rec make_rec(const Lane &p) {
@@ -377,12 +365,7 @@ __device__ void photon_event(const TransportArgs &A, const Smem &S, Lane &p, int
     int ix, iy, iz;
     const uint32_t idx = voxel_index(P, p.x, p.y, p.z, ix, iy, iz);
     const uint32_t vw = __ldg(P.vox + idx);
-    const int m = vw & 15u;
-    if (m >= NMAT) {
-        atomicExch(A.error, GPUMCD_ERR_CORRUPT);
-        p.act = false;
-        return;
-    }
+    const int m = vw & (NMAT - 1);  // ids < NMAT (checked when packed): in range by construction
     const float rho = (float)(vw >> 4) * kRhoQ;
     const float *tp = S.tab + TAB_PH + m * 3 * G;
     const bool pair_open = p.E > ph.two_mc2_q;
@@ -491,12 +474,7 @@ __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, in
     int ix, iy, iz;
     const uint32_t idx0 = voxel_index(P, p.x, p.y, p.z, ix, iy, iz);
     const uint32_t vw = __ldg(P.vox + idx0);
-    const int m0 = vw & 15u;
-    if (m0 >= NMAT) {
-        atomicExch(A.error, GPUMCD_ERR_CORRUPT);
-        p.act = false;
-        return false;
-    }
+    const int m0 = vw & (NMAT - 1);
     const float rho0 = (float)(vw >> 4) * kRhoQ;
     if (p.E < ph.e_abs_q) {
         deposit(P, p.hist, idx0, p.E);
@@ -559,12 +537,7 @@ __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, in
     if (!hard) return true;
     // electron Woodcock: accept a real hard event with Sigma(end)/Sigma_hat(start)
     const uint32_t vw1 = __ldg(P.vox + idx1);
-    const int m1 = vw1 & 15u;
-    if (m1 >= NMAT) {
-        atomicExch(A.error, GPUMCD_ERR_CORRUPT);
-        p.act = false;
-        return true;
-    }
+    const int m1 = vw1 & (NMAT - 1);
     const float rho1 = (float)(vw1 >> 4) * kRhoQ;
     const float *t1 = S.tab + TAB_EL + m1 * 4 * G;
     const float xe1 = fmaf(__log2f((float)e1), ph.grid.el_a, ph.grid.el_bq);
@@ -689,7 +662,7 @@ __device__ int refill(const TransportArgs &A, const Smem &S, CtaFlags &F, Lane &
         if (take) {
             const unsigned rank = __popc(empty & lt);
             if (!p.act && rank < take)
-                load_checked(A, p, A.stacks[((size_t)gw * 2 + t) * A.stack_cap + (sc - 1u - rank)]);
+                load_rec(p, A.stacks[((size_t)gw * 2 + t) * A.stack_cap + (sc - 1u - rank)]);
             __syncwarp();
             if (lane == 0) ws.stk[t] = sc - take;
             __syncwarp();
@@ -712,7 +685,7 @@ __device__ int refill(const TransportArgs &A, const Smem &S, CtaFlags &F, Lane &
         }
         const unsigned take = (unsigned)min((unsigned long long)__popc(empty), hi - lo);
         const unsigned rank = __popc(empty & lt);
-        if (!p.act && rank < take) load_checked(A, p, A.in[t].rec[lo + rank]);
+        if (!p.act && rank < take) load_rec(p, A.in[t].rec[lo + rank]);
         __syncwarp();
         if (lane == 0) {
             ws.q_lo[t] = lo + take;
@@ -790,7 +763,9 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-template <int MAXT, int MINB>
+// PROF compiles in the per-type cycle profile (GPUMCD_LAUNCH_PROFILE); the
+// production instantiations carry none of its code.
+template <int MAXT, int MINB, bool PROF>
 __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant__ TransportArgs A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *tab = (float *)smem_raw;
@@ -818,7 +793,9 @@ __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant_
             "l"(A.tables), "r"((uint32_t)TAB_BYTES), "r"(smem_addr(mbar))
             : "memory");
     }
-    for (int i = tid; i < A.n_plans; i += blockDim.x) plans[i] = A.plans[i];
+    // every entry is set (unused ones copy plan 0), so any masked plan index
+    // a record carries reaches valid pointers
+    for (int i = tid; i < GPUMCD_MAX_PLANS_PER_RUN; i += blockDim.x) plans[i] = A.plans[i < A.n_plans ? i : 0];
     for (int i = tid; i < MAX_WARPS; i += blockDim.x) {
         ws[i].stk[0] = ws[i].stk[1] = 0;
         ws[i].p_lo[0] = ws[i].p_hi[0] = ws[i].p_lo[1] = ws[i].p_hi[1] = 0;
@@ -852,7 +829,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant_
     p.x = p.y = p.z = p.ux = p.uy = p.uz = 0.f;
     p.E = p.hist = p.lin_lo = p.lin_hi = p.draw = p.plan = 0;
     const bool agg = (A.flags & GPUMCD_LAUNCH_WARP_AGGREGATE) != 0u;
-    const bool prof = (A.flags & GPUMCD_LAUNCH_PROFILE) != 0u;
+    constexpr bool prof = PROF;
     // start on the type that has work (electron-beam launches start on electrons)
     int t = available(A, S, F, w, 1) > available(A, S, F, w, 0) ? 1 : 0;
     unsigned iter = 0;
@@ -942,16 +919,18 @@ size_t transport_smem_bytes(int /*block_threads*/) {
 typedef void (*TransportKernel)(const TransportArgs);
 struct Variant {
     int max_threads, min_blocks;
+    bool prof;
     TransportKernel fn;
 };
 static const Variant kVariants[] = {
-    {512, 1, k_transport<512, 1>}, {384, 2, k_transport<384, 2>}, {512, 2, k_transport<512, 2>},
-    {256, 3, k_transport<256, 3>}, {256, 4, k_transport<256, 4>},
+    {512, 1, false, k_transport<512, 1, false>}, {384, 2, false, k_transport<384, 2, false>},
+    {512, 2, false, k_transport<512, 2, false>}, {256, 3, false, k_transport<256, 3, false>},
+    {256, 4, false, k_transport<256, 4, false>}, {512, 2, true, k_transport<512, 2, true>},
 };
 
-static TransportKernel pick_variant(int block, int blocks_per_sm) {
+static TransportKernel pick_variant(int block, int blocks_per_sm, bool prof) {
     for (const Variant &v : kVariants)
-        if (block <= v.max_threads && blocks_per_sm <= v.min_blocks) return v.fn;
+        if (v.prof == prof && block <= v.max_threads && blocks_per_sm <= v.min_blocks) return v.fn;
     return nullptr;
 }
 
@@ -965,7 +944,7 @@ cudaError_t transport_configure(int block_threads) {
 }
 
 cudaError_t launch_transport(const TransportArgs &a, int grid, int block, int blocks_per_sm, cudaStream_t s) {
-    TransportKernel fn = pick_variant(block, blocks_per_sm);
+    TransportKernel fn = pick_variant(block, blocks_per_sm, (a.flags & GPUMCD_LAUNCH_PROFILE) != 0u);
     if (!fn) return cudaErrorInvalidConfiguration;
     fn<<<grid, block, transport_smem_bytes(block), s>>>(a);
     return cudaGetLastError();

@@ -61,7 +61,6 @@ def test_binding_constants_match_the_header():
     for name, value in (("OK", g.OK), ("ERR_INVALID_ARG", g.ERR_INVALID_ARG), ("ERR_OOM", g.ERR_OOM),
                         ("ERR_CUDA", g.ERR_CUDA), ("ERR_QUEUE_OVERFLOW", g.ERR_QUEUE_OVERFLOW),
                         ("ERR_TIMEOUT", g.ERR_TIMEOUT), ("ERR_NOT_FOUND", g.ERR_NOT_FOUND),
-                        ("ERR_BUDGET", g.ERR_BUDGET), ("ERR_STATE", g.ERR_STATE),
-                        ("ERR_CORRUPT", g.ERR_CORRUPT)):
+                        ("ERR_BUDGET", g.ERR_BUDGET), ("ERR_STATE", g.ERR_STATE)):
         assert defs["GPUMCD_" + name] == value, name
         assert g.status_string(value) == g.STATUS[value]
