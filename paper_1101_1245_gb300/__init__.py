@@ -263,12 +263,21 @@ class Context:
 
     # ---- one-shot runs -----------------------------------------------------
     def simulate(self, pid: int, src, n_histories: int, seed: int, target_rel_unc: float = 0.0,
-                 nvox: Optional[int] = None, want_dose: bool = True) -> Result:
-        """gpumcd_simulate with host outputs."""
+                 nvox: Optional[int] = None, want_dose: bool = True, out=None) -> Result:
+        """gpumcd_simulate with host outputs: new arrays, or ``out`` = (dose, sigma),
+        two C-contiguous float64 arrays of nvox entries the caller owns (for
+        example views of pinned host memory)."""
         box = _SourceBox(src)
         st = RunStats()
-        dose = np.zeros(nvox, dtype=np.float64) if want_dose else None
-        sig = np.zeros(nvox, dtype=np.float64) if want_dose else None
+        if out is not None:
+            dose, sig = out
+            for a in (dose, sig):
+                if a.dtype != np.float64 or not a.flags.c_contiguous or (nvox and a.size != nvox):
+                    raise ValueError("out arrays must be C-contiguous float64 of nvox entries")
+            want_dose = True
+        else:
+            dose = np.zeros(nvox, dtype=np.float64) if want_dose else None
+            sig = np.zeros(nvox, dtype=np.float64) if want_dose else None
         _check(self._L.gpumcd_simulate(self.h, pid, C.byref(box.s), n_histories, seed, target_rel_unc,
                                        dose.ctypes.data if want_dose else None,
                                        sig.ctypes.data if want_dose else None, C.byref(st)),

@@ -39,6 +39,7 @@ struct Plan {
     uint64_t hist_done = 0;  // histories of completed sequences (what a fold sees)
     int inflight = 0;        // unfinished sequences that include this plan
     bool failed = false;     // a sequence failed: the tally is incomplete until plan_reset
+    cudaEvent_t reset_done = nullptr;  // after the last plan_reset's memsets (any stream)
     DevBuf tally;   // [W][nvox] u64
     DevBuf ledger;  // [4] u64
     DevBuf spec;    // [2(n_spec+1)] floats
@@ -105,6 +106,8 @@ struct gpumcd_ctx {
     cudaEvent_t order = nullptr;  // orders a submitted sequence after the context stream
     int32_t next_ticket = 1;
     DevBuf fold_tmp;
+    std::multimap<size_t, void *> cache;  // freed device blocks by size
+    uint64_t cached = 0;
     bool configured = false;
 };
 
@@ -128,18 +131,59 @@ gpumcd_status cuda_status(cudaError_t e) {
         if (s_ != GPUMCD_OK) return s_;           \
     } while (0)
 
+// Device memory is cached: a freed block goes to a size-keyed free list and
+// is handed out again for a request of up to its size (and within a quarter
+// of it, plus 1 MB), so steady-state create/open/close/destroy cycles call neither
+// cudaMalloc nor cudaFree (which synchronizes the whole device, stalling any
+// sequence in flight).  A block enters the cache only when no GPU work on it
+// is pending: every caller of dev_free has synchronized the streams that used
+// it.  The budget counts live bytes; live + cached bytes stay within it, and
+// without a budget the cache keeps at most kCacheMax bytes.
+constexpr uint64_t kCacheMax = 32ull << 30;
+
+void cache_trim(gpumcd_ctx *c, uint64_t limit) {
+    while (c->cached > limit && !c->cache.empty()) {
+        auto it = std::prev(c->cache.end());  // largest block first
+        cudaFree(it->second);
+        c->cached -= it->first;
+        c->cache.erase(it);
+    }
+}
+
+void dev_free(gpumcd_ctx *c, DevBuf &b) {
+    if (b.p) {
+        c->used -= b.bytes;
+        c->cache.emplace(b.bytes, b.p);
+        c->cached += b.bytes;
+        if (c->budget) cache_trim(c, c->budget > c->used ? c->budget - c->used : 0);
+        else cache_trim(c, kCacheMax);
+    }
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
 gpumcd_status dev_alloc(gpumcd_ctx *c, DevBuf &b, size_t bytes) {
     if (b.p && b.bytes >= bytes) return GPUMCD_OK;
-    size_t freed = b.bytes;
-    if (c->budget && c->used - freed + bytes > c->budget) return GPUMCD_ERR_BUDGET;
-    if (b.p) {
-        cudaFree(b.p);
-        c->used -= b.bytes;
-        b.p = nullptr;
-        b.bytes = 0;
-    }
+    if (c->budget && c->used - b.bytes + bytes > c->budget) return GPUMCD_ERR_BUDGET;
+    dev_free(c, b);
     if (bytes == 0) return GPUMCD_OK;
+    auto it = c->cache.lower_bound(bytes);
+    if (it != c->cache.end() && it->first <= bytes + bytes / 4 + (1u << 20) &&
+        (!c->budget || c->used + it->first <= c->budget)) {
+        b.p = it->second;
+        b.bytes = it->first;
+        c->cached -= it->first;
+        c->cache.erase(it);
+        c->used += b.bytes;
+        return GPUMCD_OK;
+    }
+    if (c->budget) cache_trim(c, c->budget - c->used - bytes);
     cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e == cudaErrorMemoryAllocation && c->cached) {
+        cudaGetLastError();
+        cache_trim(c, 0);
+        e = cudaMalloc(&b.p, bytes);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         b.p = nullptr;
@@ -148,15 +192,6 @@ gpumcd_status dev_alloc(gpumcd_ctx *c, DevBuf &b, size_t bytes) {
     b.bytes = bytes;
     c->used += bytes;
     return GPUMCD_OK;
-}
-
-void dev_free(gpumcd_ctx *c, DevBuf &b) {
-    if (b.p) {
-        cudaFree(b.p);
-        c->used -= b.bytes;
-    }
-    b.p = nullptr;
-    b.bytes = 0;
 }
 
 cudaStream_t pick(gpumcd_ctx *c, void *stream) { return stream ? (cudaStream_t)stream : c->stream; }
@@ -309,6 +344,7 @@ gpumcd_status gpumcd_destroy(gpumcd_ctx *c) {
     for (Slot &sl : c->slot)
         if (sl.busy && sl.s) cudaStreamSynchronize(sl.s);
     for (auto &kv : c->plans) {
+        if (kv.second.reset_done) cudaEventDestroy(kv.second.reset_done);
         dev_free(c, kv.second.tally);
         dev_free(c, kv.second.ledger);
         dev_free(c, kv.second.spec);
@@ -321,6 +357,7 @@ gpumcd_status gpumcd_destroy(gpumcd_ctx *c) {
     dev_free(c, c->tab);
     for (Slot &sl : c->slot) free_slot(c, sl);
     dev_free(c, c->fold_tmp);
+    cache_trim(c, 0);
     if (c->order) cudaEventDestroy(c->order);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -500,8 +537,8 @@ gpumcd_status gpumcd_plan_open(gpumcd_ctx *c, int32_t phantom_id, const gpumcd_s
     }
     dev_free(c, tmp);
     if (st == GPUMCD_OK) {
-        cudaError_t e = cudaMemsetAsync(p.tally.p, 0, p.tally.bytes, c->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(p.ledger.p, 0, p.ledger.bytes, c->stream);
+        cudaError_t e = cudaMemsetAsync(p.tally.p, 0, (size_t)n_batches * nvox * 8, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p.ledger.p, 0, 4 * 8, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) st = cuda_status(e);
     }
@@ -510,6 +547,13 @@ gpumcd_status gpumcd_plan_open(gpumcd_ctx *c, int32_t phantom_id, const gpumcd_s
         dev_free(c, p.ledger);
         dev_free(c, p.spec);
         return st;
+    }
+    if (cudaEventCreateWithFlags(&p.reset_done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        dev_free(c, p.tally);
+        dev_free(c, p.ledger);
+        dev_free(c, p.spec);
+        return GPUMCD_ERR_CUDA;
     }
     *plan_id = c->next_id++;
     c->plans[*plan_id] = p;
@@ -522,7 +566,13 @@ gpumcd_status gpumcd_plan_close(gpumcd_ctx *c, int32_t plan_id) {
     if (it == c->plans.end()) return GPUMCD_ERR_NOT_FOUND;
     if (it->second.inflight > 0) return GPUMCD_ERR_STATE;
     ST(set_device(c));
+    // the tally goes back to the cache: wait for the context stream and for
+    // the last reset's memsets, which may have run on a caller's stream
     cudaStreamSynchronize(c->stream);
+    if (it->second.reset_done) {
+        cudaEventSynchronize(it->second.reset_done);
+        cudaEventDestroy(it->second.reset_done);
+    }
     dev_free(c, it->second.tally);
     dev_free(c, it->second.ledger);
     dev_free(c, it->second.spec);
@@ -538,8 +588,10 @@ gpumcd_status gpumcd_plan_reset(gpumcd_ctx *c, int32_t plan_id, uint64_t seed, v
     ST(set_device(c));
     cudaStream_t s = pick(c, stream);
     Plan &p = it->second;
-    CK(cudaMemsetAsync(p.tally.p, 0, p.tally.bytes, s));
-    CK(cudaMemsetAsync(p.ledger.p, 0, p.ledger.bytes, s));
+    // a cached block may be larger than the tally: zero the tally's own size
+    CK(cudaMemsetAsync(p.tally.p, 0, (size_t)p.W * c->phantoms.at(p.phantom).nvox * 8, s));
+    CK(cudaMemsetAsync(p.ledger.p, 0, 4 * 8, s));
+    CK(cudaEventRecord(p.reset_done, s));
     p.seed = seed;
     p.hist_sub = 0;
     p.hist_done = 0;

@@ -119,3 +119,42 @@ def test_hbm_budget_is_enforced():
     used, budget = c.memory()
     assert used <= budget == 64 << 20
     c.close()
+
+
+def test_device_memory_is_reused():
+    """Phantom, plan and scratch blocks return to the context's cache and are
+    handed out again: live memory stays flat over create/simulate/destroy
+    cycles and the results do not change."""
+    ctx = make_ctx()
+    ph = W.homogeneous((40, 36, 32), 0.5, W.MAT_WATER, 1.0)
+    src = W.square_field(W.PHOTON, 6.0, ph, 6.0)
+    doses, used = [], []
+    for i in range(4):
+        pid = ctx.create_phantom(ph)
+        r = ctx.simulate(pid, src, 20_000, 5, nvox=ph.nvox)
+        doses.append(r.dose)
+        ctx.destroy_phantom(pid)
+        used.append(ctx.memory()[0])
+    assert used[1] == used[2] == used[3]
+    assert all(np.array_equal(doses[0], d) for d in doses[1:])
+    ctx.close()
+
+
+def test_cached_blocks_yield_to_the_budget():
+    """Blocks in the cache are released when a new allocation needs the room."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = g.Context(0, hbm_budget_bytes=200 << 20)
+    c.load_materials(W.MATERIALS, W.DEFAULT_PHYSICS)
+    small = c.create_phantom(W.homogeneous((64, 64, 64), 0.5, W.MAT_WATER, 1.0))  # 1 MB
+    big = c.plan_open(small, W.pencil(W.PHOTON, 1.0, 16, 16), 1, 64)  # 134 MB of tallies
+    c.plan_close(big)  # -> cache
+    ph2 = W.homogeneous((96, 96, 64), 0.5, W.MAT_WATER, 1.0)  # 2.4 MB
+    pid2 = c.create_phantom(ph2)
+    p2 = c.plan_open(pid2, W.pencil(W.PHOTON, 1.0, 24, 24), 1, 32)  # 151 MB: the cached block must go
+    assert c.plan_histories(p2) == 0
+    used, budget = c.memory()
+    assert used <= budget
+    c.plan_close(p2)
+    c.close()
