@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--graph", action="store_true",
                     help="launch each sequence's first launch from a captured CUDA graph")
     ap.add_argument("--requests", type=int, default=1000, help="served: number of requests")
+    ap.add_argument("--round-histories", type=int, default=16_000_000,
+                    help="served: histories per round over all active plans")
+    ap.add_argument("--rounds-in-flight", type=int, default=2, help="served: rounds on the device at once")
     ap.add_argument("--calibration", type=int, default=48,
                     help="served: requests of the capacity run (served vs alone)")
     ap.add_argument("--target", type=float, default=0.01, help="served: relative uncertainty target")
@@ -432,7 +435,8 @@ def run_served(args):
     # capacity: a calibration set all present at once, served, against the
     # same requests run one at a time with the plain kernel
     cal = requests(1.0)[:min(args.calibration, args.requests)]
-    srv = Server(ctx, budget, target=args.target)
+    srv = Server(ctx, budget, target=args.target, round_histories=args.round_histories,
+                 rounds_in_flight=args.rounds_in_flight)
     for q in cal:
         srv.submit(q)
     srv.run(real_time=False)
@@ -443,7 +447,8 @@ def run_served(args):
     mean_h = rep_cal["histories"] / max(rep_cal["requests"], 1)
     rate = 0.8 * rep_cal["histories_per_s"] / mean_h
     # the stream: Poisson arrivals at 0.8 x that capacity
-    srv = Server(ctx, budget, target=args.target)
+    srv = Server(ctx, budget, target=args.target, round_histories=args.round_histories,
+                 rounds_in_flight=args.rounds_in_flight)
     reqs = requests(rate)
     for q in reqs:
         srv.submit(q)
@@ -461,7 +466,8 @@ def run_served(args):
           "stream_value": rep["histories_per_s"], "latency_p50_s": rep["latency_p50_s"],
           "latency_p99_s": rep["latency_p99_s"], "wall_s": rep["wall_s"], "rounds": rep["rounds"],
           "folds": rep["folds"], "mean_histories_per_request": rep["histories"] / max(rep["requests"], 1),
-          "s_thr_max": rep["s_thr_max"], "rounds_in_flight": g.MAX_INFLIGHT, "hbm_budget_gb": args.budget_gb,
+          "s_thr_max": rep["s_thr_max"], "rounds_in_flight": args.rounds_in_flight,
+          "round_histories": args.round_histories, "hbm_budget_gb": args.budget_gb,
           "launch_graph": bool(args.graph),
           "phantoms": "64 resident config-4 phantoms, request i on phantom i mod 64", "data": "synthetic"})
     ctx.close()

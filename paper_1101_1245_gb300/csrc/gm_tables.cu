@@ -363,9 +363,18 @@ __device__ __forceinline__ double u128_to_double(U128 v) {
     return (double)v.hi * 18446744073709551616.0 + (double)v.lo;
 }
 
+// FP64 is scarce on GB300, so the per-voxel FP64 work is one division (by
+// the voxel's density code, shared by dose and sigma) and one square root;
+// the other divisors are loop constants whose reciprocals come from the host.
+struct FoldConst {
+    double inv_n;   // 1 / N
+    double c_var;   // 1 / (W^2 (W - 1) n^2), n = N / W
+    double k_dose;  // q * (MeV/g -> Gy) / (voxel volume * density quantum)
+};
+
 template <int W>
-__global__ void k_fold_equal(const unsigned long long *tally, const uint32_t *vox, uint64_t nvox, double n_tot,
-                             double inv_vol, double *dose, double *sigma, unsigned long long *dmax_bits,
+__global__ void k_fold_equal(const unsigned long long *tally, const uint32_t *vox, uint64_t nvox, FoldConst fc,
+                             double *dose, double *sigma, unsigned long long *dmax_bits,
                              unsigned long long *dep_sum) {
     double local_max = 0.0;
     unsigned long long local_sum = 0;
@@ -380,29 +389,27 @@ __global__ void k_fold_equal(const unsigned long long *tally, const uint32_t *vo
             tot += s[b];
             add_sq(sq, s[b]);
         }
-        const double mean = (double)tot / n_tot;
-        const double n = n_tot / (double)W;
-        double var;
+        double var_sum;  // sum_b (S_b - S/W)^2, in quanta^2
         if (sq.hi < (1ull << 57)) {
-            // W sum S_b^2 - S^2, exact and non-negative (Cauchy-Schwarz); then
-            // var(D) = sum_b (S_b - S/W)^2 / (W (W - 1) n^2) = num / (W^2 (W - 1) n^2)
+            // W sum S_b^2 - S^2, exact and non-negative (Cauchy-Schwarz), = W var_sum
             const U128 ws{sq.lo * (unsigned long long)W, sq.hi * (unsigned long long)W + __umul64hi(sq.lo, (unsigned long long)W)};
             const U128 t2{tot * tot, __umul64hi(tot, tot)};
             const U128 num{ws.lo - t2.lo, ws.hi - t2.hi - (ws.lo < t2.lo ? 1ull : 0ull)};
-            var = u128_to_double(num) / ((double)W * (double)W * (double)(W - 1) * n * n);
+            var_sum = u128_to_double(num) * (1.0 / (double)W);
         } else {
+            const double m = (double)tot * (1.0 / (double)W);
             double acc = 0.0;
             for (int b = 0; b < W; ++b) {
-                const double t = fma(-n, mean, (double)s[b]);
+                const double t = (double)s[b] - m;
                 acc = fma(t, t, acc);
             }
-            var = acc * ((double)W / ((double)(W - 1) * n_tot * n_tot));
+            var_sum = acc;
         }
-        const double rho = (double)(vox[v] >> 4) * (double)kRhoQ;
-        const double scale = kQ * kMeVPerGramToGy * inv_vol / rho;
-        const double dv = mean * scale;
+        // var(D) = var_sum / (W (W - 1) n^2) in quanta^2 per history^2
+        const double r = fc.k_dose / (double)(vox[v] >> 4);
+        const double dv = (double)tot * fc.inv_n * r;
         if (dose) dose[v] = dv;
-        if (sigma) sigma[v] = sqrt(var) * scale;
+        if (sigma) sigma[v] = sqrt(var_sum * ((double)W * fc.c_var)) * r;
         local_max = fmax(local_max, dv);
         local_sum += tot;
     }
@@ -536,11 +543,16 @@ cudaError_t launch_fold(const unsigned long long *tally, const uint32_t *vox, ui
     const uint64_t cap = (uint64_t)n_sm * 8;
     const int grid = (int)(blocks < cap ? (blocks ? blocks : 1) : cap);
     if (equal) {
+        FoldConst fc;
+        const double n = n_tot / (double)W;
+        fc.inv_n = 1.0 / n_tot;
+        fc.c_var = 1.0 / ((double)W * (double)W * (double)(W - 1) * n * n);
+        fc.k_dose = kQ * kMeVPerGramToGy * inv_vol / kRhoQ;
         switch (W) {
-            case 8: k_fold_equal<8><<<grid, 256, 0, s>>>(tally, vox, nvox, n_tot, inv_vol, dose, sigma, dmax_bits, dep_sum); break;
-            case 16: k_fold_equal<16><<<grid, 256, 0, s>>>(tally, vox, nvox, n_tot, inv_vol, dose, sigma, dmax_bits, dep_sum); break;
-            case 32: k_fold_equal<32><<<grid, 256, 0, s>>>(tally, vox, nvox, n_tot, inv_vol, dose, sigma, dmax_bits, dep_sum); break;
-            case 64: k_fold_equal<64><<<grid, 256, 0, s>>>(tally, vox, nvox, n_tot, inv_vol, dose, sigma, dmax_bits, dep_sum); break;
+            case 8: k_fold_equal<8><<<grid, 256, 0, s>>>(tally, vox, nvox, fc, dose, sigma, dmax_bits, dep_sum); break;
+            case 16: k_fold_equal<16><<<grid, 256, 0, s>>>(tally, vox, nvox, fc, dose, sigma, dmax_bits, dep_sum); break;
+            case 32: k_fold_equal<32><<<grid, 256, 0, s>>>(tally, vox, nvox, fc, dose, sigma, dmax_bits, dep_sum); break;
+            case 64: k_fold_equal<64><<<grid, 256, 0, s>>>(tally, vox, nvox, fc, dose, sigma, dmax_bits, dep_sum); break;
             default: return cudaErrorInvalidValue;
         }
         return cudaGetLastError();

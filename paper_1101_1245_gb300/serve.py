@@ -86,12 +86,14 @@ class Server:
     round_histories  histories per round over all active plans
     first_chunk   histories of a new plan's first round
     hbm_budget    bytes of tallies the server may hold at once
+    rounds_in_flight  rounds on the device at once (1 .. MAX_INFLIGHT)
     """
 
     def __init__(self, ctx: Context, hbm_budget: int, target: float = 0.01,
                  threshold: float = 0.5, n_batches: int = 16,
-                 round_histories: int = 4_000_000, first_chunk: int = 200_000,
-                 keep_dose: bool = False, clock: Callable[[], float] = time.perf_counter):
+                 round_histories: int = 16_000_000, first_chunk: int = 200_000,
+                 keep_dose: bool = False, clock: Callable[[], float] = time.perf_counter,
+                 rounds_in_flight: int = MAX_INFLIGHT):
         self.ctx = ctx
         self.budget = hbm_budget
         self.target = target
@@ -101,6 +103,9 @@ class Server:
         self.first_chunk = first_chunk
         self.keep_dose = keep_dose
         self.clock = clock
+        if not 1 <= rounds_in_flight <= MAX_INFLIGHT:
+            raise ValueError(f"rounds_in_flight must be in [1, {MAX_INFLIGHT}]")
+        self.depth = rounds_in_flight
         self.used = 0
         self.waiting: List[tuple] = []  # heap of (arrival, rid, request)
         self.active: Dict[int, _Active] = {}
@@ -163,7 +168,7 @@ class Server:
 
     def _submit_rounds(self) -> None:
         """Fill the free launch slots with rounds over the plans that have work."""
-        while len(self.inflight) < MAX_INFLIGHT:
+        while len(self.inflight) < self.depth:
             plans = self._runnable()
             if not plans:
                 return
