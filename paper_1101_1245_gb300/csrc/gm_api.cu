@@ -60,7 +60,7 @@ struct Control {
 // gpumcd_run on the caller's stream; slots 1..GPUMCD_MAX_INFLIGHT serve
 // gpumcd_submit on their own streams, so sequences can overlap on the device.
 struct Slot {
-    DevBuf stacks, queue[2][NT], control, plandev;
+    DevBuf stacks, hard, queue[2][NT], control, plandev;
     Control *h_control = nullptr;  // pinned: the control block after each launch
     PlanDev *h_plandev = nullptr;  // pinned: the sequence's plan table
     cudaStream_t own = nullptr;    // the slot's stream (asynchronous slots)
@@ -222,6 +222,7 @@ bool valid_source(const gpumcd_ctx *c, const gpumcd_source *s) {
 gpumcd_status ensure_slot(gpumcd_ctx *c, Slot &sl, int grid, int block) {
     const size_t warps = (size_t)grid * (block / 32);
     ST(dev_alloc(c, sl.stacks, warps * NT * c->launch.stack_capacity * sizeof(Rec)));
+    ST(dev_alloc(c, sl.hard, warps * HARD_CAP * sizeof(HardRec)));
     for (int b = 0; b < 2; ++b)
         for (int t = 0; t < NT; ++t)
             ST(dev_alloc(c, sl.queue[b][t], (size_t)c->launch.overflow_capacity * sizeof(Rec)));
@@ -242,6 +243,7 @@ gpumcd_status ensure_slot(gpumcd_ctx *c, Slot &sl, int grid, int block) {
 void free_slot(gpumcd_ctx *c, Slot &sl) {
     if (sl.busy && sl.s) cudaStreamSynchronize(sl.s);
     dev_free(c, sl.stacks);
+    dev_free(c, sl.hard);
     for (int b = 0; b < 2; ++b)
         for (int t = 0; t < NT; ++t) dev_free(c, sl.queue[b][t]);
     dev_free(c, sl.control);
@@ -820,6 +822,7 @@ gpumcd_status seq_start(gpumcd_ctx *c, Slot &sl, int32_t n_plans, const int32_t 
     A.n_plans = n_plans;
     A.prim_cursor = dc->prim_cursor;
     A.stacks = (Rec *)sl.stacks.p;
+    A.hard = (HardRec *)sl.hard.p;
     A.stack_cap = c->launch.stack_capacity;
     A.switch_high = c->launch.switch_high;
     A.refill_low = c->launch.refill_low;

@@ -72,6 +72,18 @@ struct __align__(16) Rec {
     uint4 c;
 };
 
+// An electron whose step ended on a hard-event candidate (§II.B.3, the
+// electron Woodcock test), parked until its warp runs a converged hard pass:
+// the particle after its step, the majorant Sigma_hat of the step's start
+// energy and the voxel of the end point.  64 bytes.
+struct __align__(16) HardRec {
+    Rec r;
+    float sig_hat;
+    uint32_t idx;
+    uint32_t pad[2];
+};
+constexpr unsigned HARD_CAP = 64;  // per warp: a pass starts at 32, one step adds at most 32
+
 // One plan inside a launch (copied to shared memory by the transport kernel).
 struct __align__(16) PlanDev {
     const uint32_t *vox;           // packed voxel words
@@ -111,6 +123,7 @@ struct TransportArgs {
     Queue in[NT], out[NT];
     unsigned long long in_count[NT];   // records available in in[t]
     Rec *stacks;                       // [warp][type][stack_capacity]
+    HardRec *hard;                     // [warp][HARD_CAP] parked hard-event candidates
     uint32_t stack_cap, switch_high, refill_low, chunk;
     uint32_t flags;
     unsigned long long *counters;      // run counters (see CNT_*)
@@ -126,7 +139,9 @@ enum {
     // the active lanes summed over them; then cycles in refills and the number
     // of type switches
     CNT_PROF_CYC, CNT_PROF_ITER = CNT_PROF_CYC + NT, CNT_PROF_LANES = CNT_PROF_ITER + NT,
-    CNT_PROF_REFILL_CYC = CNT_PROF_LANES + NT, CNT_PROF_SWITCHES, CNT_N
+    CNT_PROF_REFILL_CYC = CNT_PROF_LANES + NT, CNT_PROF_SWITCHES,
+    // converged passes over parked hard-event candidates (always counted)
+    CNT_HARD_PASSES, CNT_N
 };
 
 // ---------------------------------------------------------------------------

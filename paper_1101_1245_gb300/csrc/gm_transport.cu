@@ -25,7 +25,8 @@ constexpr int MAX_WARPS = 32;
 
 struct WarpState {
     unsigned int stk[2];
-    unsigned int pad[2];
+    unsigned int hc;   // parked hard-event candidates (electrons)
+    unsigned int pad;
     unsigned long long p_lo[2], p_hi[2];  // claimed primaries by type (type-local index)
     unsigned long long q_lo[2], q_hi[2];  // claimed overflow-queue records by type
 };
@@ -535,6 +536,31 @@ __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, in
         return true;
     }
     if (!hard) return true;
+    // A hard-event candidate: park the particle for a converged hard pass of
+    // its warp (the candidate test and the event follow there, with the same
+    // random draws in the same order, so the result does not change).
+    {
+        const unsigned slot = atomicAdd(&S.ws[w].hc, 1u);
+        HardRec &h = A.hard[(size_t)gw * HARD_CAP + slot];
+        h.r = make_rec(p);
+        h.sig_hat = sig_hat;
+        h.idx = idx1;
+        p.act = false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Electron hard event (GPUMCD §II.B.3): the electron Woodcock test at the end
+// of a step whose sampled hard distance was the shortest, then Moller or
+// bremsstrahlung.  Runs in the warp's hard pass with the parked candidate in
+// the lane: p after its step, sig_hat = Sigma_hat(E0), idx1 = its voxel.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void hard_event(const TransportArgs &A, const Smem &S, Lane &p, float sig_hat,
+                                        uint32_t idx1, int gw, int w) {
+    const PlanDev &P = S.plans[p.plan];
+    const Phys &ph = A.phys;
+    const uint32_t e1 = p.E;
     // electron Woodcock: accept a real hard event with Sigma(end)/Sigma_hat(start)
     const uint32_t vw1 = __ldg(P.vox + idx1);
     const int m1 = vw1 & (NMAT - 1);
@@ -550,7 +576,7 @@ __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, in
     const uint4 r2 = draw4(p, P);
     if (u01(r2.x) * sig_hat >= sig) {
         count(S, CNT_HARD_FICT);
-        return true;
+        return;
     }
     count(S, CNT_HARD_REAL);
     if (u01(r2.y) * sig < sm) {
@@ -596,7 +622,6 @@ __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, in
             deposit(P, p.hist, idx1, kq);
         p.E = e1 - kq;
     }
-    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -741,7 +766,7 @@ __device__ __forceinline__ unsigned available(const TransportArgs &A, const Smem
     unsigned n = 0;
     if ((threadIdx.x & 31) == 0) {
         const WarpState &ws = S.ws[w];
-        n = ws.stk[t];
+        n = ws.stk[t] + (t == 1 ? ws.hc : 0u);  // parked hard candidates are electrons
         if (ws.q_lo[t] < ws.q_hi[t]) n += 32;
         else if (!*(volatile int *)&F.in_done[t]) {
             if (*(volatile unsigned long long *)A.in[t].cursor < A.in_count[t]) n += 32;
@@ -754,6 +779,45 @@ __device__ __forceinline__ unsigned available(const TransportArgs &A, const Smem
         }
     }
     return __shfl_sync(FULL, n, 0);
+}
+
+// The warp's hard pass: park its stepping electrons on their stack, take up
+// to 32 parked hard-event candidates into the lanes and run their events
+// together.  The lanes then hold electrons again (after their events), so
+// the warp goes on stepping electrons.
+__device__ __forceinline__ void hard_pass(const TransportArgs &A, const Smem &S, Lane &p, int gw, int w) {
+    const int lane = threadIdx.x & 31;
+    if (S.ws[w].stk[1] + 32u > A.stack_cap) spill_to_queue(A, S, gw, w, 1, 64u);
+    const unsigned actm = __ballot_sync(FULL, p.act);
+    const unsigned base = S.ws[w].stk[1];
+    if (p.act) {
+        const unsigned rank = __popc(actm & lanemask_lt());
+        A.stacks[((size_t)gw * 2 + 1) * A.stack_cap + base + rank] = make_rec(p);
+        p.act = false;
+    }
+    __syncwarp();
+    const unsigned hc = S.ws[w].hc;
+    const unsigned take = min(32u, hc);
+    float sig_hat = 0.f;
+    uint32_t idx1 = 0u;
+    if ((unsigned)lane < take) {
+        const HardRec &h = A.hard[(size_t)gw * HARD_CAP + (hc - 1u - lane)];
+        load_rec(p, h.r);
+        sig_hat = h.sig_hat;
+        idx1 = h.idx;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        S.ws[w].stk[1] = base + __popc(actm);
+        S.ws[w].hc = hc - take;
+        atomicAdd(&S.cnt[CNT_HARD_PASSES], 1ull);
+    }
+    __syncwarp();
+    // headroom for the events' secondaries (at most one per lane per type)
+    if (S.ws[w].stk[0] + 64u > A.stack_cap) spill_to_queue(A, S, gw, w, 0, 64u);
+    if (S.ws[w].stk[1] + 64u > A.stack_cap) spill_to_queue(A, S, gw, w, 1, 64u);
+    if (p.act) hard_event(A, S, p, sig_hat, idx1, gw, w);
+    __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
@@ -798,6 +862,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant_
     for (int i = tid; i < GPUMCD_MAX_PLANS_PER_RUN; i += blockDim.x) plans[i] = A.plans[i < A.n_plans ? i : 0];
     for (int i = tid; i < MAX_WARPS; i += blockDim.x) {
         ws[i].stk[0] = ws[i].stk[1] = 0;
+        ws[i].hc = 0;
         ws[i].p_lo[0] = ws[i].p_hi[0] = ws[i].p_lo[1] = ws[i].p_hi[1] = 0;
         ws[i].q_lo[0] = ws[i].q_hi[0] = ws[i].q_lo[1] = ws[i].q_hi[1] = 0;
     }
@@ -848,6 +913,16 @@ __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant_
         const int n_act = refill(A, S, F, p, gw, w, t);
         if (prof && lane == 0) atomicAdd(&S.cnt[CNT_PROF_REFILL_CYC], (unsigned long long)(clock64() - c0));
         const int o = 1 - t;
+        // electrons: a converged hard pass once 32 candidates are parked (a
+        // step parks at most 32 more, within HARD_CAP), or sooner when the
+        // warp has few electrons left to step
+        if (t == 1) {
+            const unsigned hc = S.ws[w].hc;
+            if (hc >= 32u || (hc > 0u && n_act < (int)A.refill_low)) {
+                hard_pass(A, S, p, gw, w);
+                continue;
+            }
+        }
         if (n_act == 0) {
             if (available(A, S, F, w, o) > 0u) {
                 t = o;
