@@ -918,7 +918,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant_
         // warp has few electrons left to step
         if (t == 1) {
             const unsigned hc = S.ws[w].hc;
-            if (hc >= 32u || (hc > 0u && n_act < (int)A.refill_low)) {
+            // (n_act == 0 also when refill_low is 0: parked candidates must not be left behind)
+            if (hc >= 32u || (hc > 0u && (n_act == 0 || n_act < (int)A.refill_low))) {
                 hard_pass(A, S, p, gw, w);
                 continue;
             }
