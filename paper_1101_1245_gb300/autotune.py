@@ -20,7 +20,7 @@ from . import Context
 SHAPES: List[Tuple[int, int]] = [(512, 2), (384, 2), (256, 3), (512, 1)]
 KNOBS: Dict[str, List[int]] = {
     "chunk": [16, 32, 64],
-    "switch_high": [128, 200, 320],
+    "switch_high": [200, 320, 384],
     "refill_low": [8, 16, 24],
 }
 

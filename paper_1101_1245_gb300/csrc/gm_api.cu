@@ -330,7 +330,7 @@ gpumcd_status gpumcd_init(gpumcd_ctx **out, int32_t device, uint64_t hbm_budget_
     c->launch.block_threads = 512;
     c->launch.blocks_per_sm = 2;
     c->launch.stack_capacity = 512;
-    c->launch.switch_high = 200;
+    c->launch.switch_high = 320;
     c->launch.refill_low = 16;
     c->launch.chunk = 32;
     c->launch.overflow_capacity = 1u << 20;
