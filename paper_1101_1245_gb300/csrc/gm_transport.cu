@@ -11,6 +11,10 @@
 // and spill to a global overflow queue only when a stack fills; a warp
 // switches type when its own lanes run dry or when the other stack is high
 // (§II.C.3's "pool" of persistent threads, with warp-uniform particle type).
+// An electron step that ends on a hard-event candidate parks the particle on
+// a third per-warp stack; with 32 parked, the warp runs their Woodcock tests
+// and Moller/bremsstrahlung events together (a converged hard pass) instead
+// of one or two lanes at a time inside every step.
 //
 // Randomness is a counter-based Philox keyed by the plan seed with counter
 // (draw, lineage lo, lineage hi, history), and energies are integers, so the
