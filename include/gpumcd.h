@@ -108,6 +108,8 @@ typedef struct {
 
 #define GPUMCD_LAUNCH_WARP_AGGREGATE 1u /* combine a warp's deposits to one voxel into one atomic */
 #define GPUMCD_LAUNCH_PROFILE 2u        /* count clock cycles per event type (see gpumcd_debug_counters) */
+/* The two flags above select separately compiled kernels: each needs blocks_per_sm <= 2, and
+ * they cannot be combined (GPUMCD_ERR_INVALID_ARG). */
 #define GPUMCD_LAUNCH_GRAPH 4u          /* replay a sequence's first launch from a captured CUDA graph */
 
 /* Counters of one run.  The ledger satisfies, exactly,

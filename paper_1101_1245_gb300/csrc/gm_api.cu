@@ -1139,8 +1139,11 @@ gpumcd_status gpumcd_set_launch(gpumcd_ctx *c, const gpumcd_launch *l) {
     if (n.switch_high < 32 || n.switch_high > n.stack_capacity) return GPUMCD_ERR_INVALID_ARG;
     if (n.refill_low > 32 || n.chunk < 1 || n.chunk > 4096) return GPUMCD_ERR_INVALID_ARG;
     if (n.overflow_capacity < 64 || n.overflow_capacity > (1u << 26)) return GPUMCD_ERR_INVALID_ARG;
-    // the profiling kernel is instantiated for up to 512 threads x 2 CTAs per SM
-    if ((n.flags & GPUMCD_LAUNCH_PROFILE) && n.blocks_per_sm > 2) return GPUMCD_ERR_INVALID_ARG;
+    // the profiling and warp-aggregating kernels are instantiated for up to
+    // 512 threads x 2 CTAs per SM, and not together
+    if ((n.flags & (GPUMCD_LAUNCH_PROFILE | GPUMCD_LAUNCH_WARP_AGGREGATE)) && n.blocks_per_sm > 2)
+        return GPUMCD_ERR_INVALID_ARG;
+    if ((n.flags & GPUMCD_LAUNCH_PROFILE) && (n.flags & GPUMCD_LAUNCH_WARP_AGGREGATE)) return GPUMCD_ERR_INVALID_ARG;
     c->launch = n;
     return GPUMCD_OK;
 }

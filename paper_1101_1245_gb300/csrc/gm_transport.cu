@@ -831,9 +831,10 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// PROF compiles in the per-type cycle profile (GPUMCD_LAUNCH_PROFILE); the
-// production instantiations carry none of its code.
-template <int MAXT, int MINB, bool PROF>
+// PROF compiles in the per-type cycle profile (GPUMCD_LAUNCH_PROFILE) and AGG
+// the warp-aggregated deposit (GPUMCD_LAUNCH_WARP_AGGREGATE); the production
+// instantiations carry neither.
+template <int MAXT, int MINB, bool PROF, bool AGG>
 __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant__ TransportArgs A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *tab = (float *)smem_raw;
@@ -897,7 +898,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant_
     p.act = false;
     p.x = p.y = p.z = p.ux = p.uy = p.uz = 0.f;
     p.E = p.hist = p.lin_lo = p.lin_hi = p.draw = p.plan = 0;
-    const bool agg = (A.flags & GPUMCD_LAUNCH_WARP_AGGREGATE) != 0u;
+    constexpr bool agg = AGG;
     constexpr bool prof = PROF;
     // start on the type that has work (electron-beam launches start on electrons)
     int t = available(A, S, F, w, 1) > available(A, S, F, w, 0) ? 1 : 0;
@@ -999,18 +1000,23 @@ size_t transport_smem_bytes(int /*block_threads*/) {
 typedef void (*TransportKernel)(const TransportArgs);
 struct Variant {
     int max_threads, min_blocks;
-    bool prof;
+    bool prof, agg;
     TransportKernel fn;
 };
 static const Variant kVariants[] = {
-    {512, 1, false, k_transport<512, 1, false>}, {384, 2, false, k_transport<384, 2, false>},
-    {512, 2, false, k_transport<512, 2, false>}, {256, 3, false, k_transport<256, 3, false>},
-    {256, 4, false, k_transport<256, 4, false>}, {512, 2, true, k_transport<512, 2, true>},
+    {512, 1, false, false, k_transport<512, 1, false, false>},
+    {384, 2, false, false, k_transport<384, 2, false, false>},
+    {512, 2, false, false, k_transport<512, 2, false, false>},
+    {256, 3, false, false, k_transport<256, 3, false, false>},
+    {256, 4, false, false, k_transport<256, 4, false, false>},
+    {512, 2, true, false, k_transport<512, 2, true, false>},
+    {512, 2, false, true, k_transport<512, 2, false, true>},
 };
 
-static TransportKernel pick_variant(int block, int blocks_per_sm, bool prof) {
+static TransportKernel pick_variant(int block, int blocks_per_sm, bool prof, bool agg) {
     for (const Variant &v : kVariants)
-        if (v.prof == prof && block <= v.max_threads && blocks_per_sm <= v.min_blocks) return v.fn;
+        if (v.prof == prof && v.agg == agg && block <= v.max_threads && blocks_per_sm <= v.min_blocks)
+            return v.fn;
     return nullptr;
 }
 
@@ -1024,7 +1030,8 @@ cudaError_t transport_configure(int block_threads) {
 }
 
 cudaError_t launch_transport(const TransportArgs &a, int grid, int block, int blocks_per_sm, cudaStream_t s) {
-    TransportKernel fn = pick_variant(block, blocks_per_sm, (a.flags & GPUMCD_LAUNCH_PROFILE) != 0u);
+    TransportKernel fn = pick_variant(block, blocks_per_sm, (a.flags & GPUMCD_LAUNCH_PROFILE) != 0u,
+                                      (a.flags & GPUMCD_LAUNCH_WARP_AGGREGATE) != 0u);
     if (!fn) return cudaErrorInvalidConfiguration;
     fn<<<grid, block, transport_smem_bytes(block), s>>>(a);
     return cudaGetLastError();
