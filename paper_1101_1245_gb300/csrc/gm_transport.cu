@@ -340,9 +340,14 @@ __device__ __forceinline__ uint32_t make_primary(Lane &p, const PlanDev &P, uint
 }
 
 // ---------------------------------------------------------------------------
-// Photon: one Woodcock flight and, if real, the interaction (GPUMCD §II.A)
+// Photon transport
 // ---------------------------------------------------------------------------
-__device__ void photon_event(const TransportArgs &A, const Smem &S, Lane &p, int gw, int w) {
+// Photon (GPUMCD §II.A).  photon_flight: one Woodcock flight; true when it
+// ends on a real event, with its voxel and the word that picks the
+// interaction.  photon_interact: that interaction (Compton, photoelectric or
+// pair, by the partial attenuation coefficients of the voxel's material).
+__device__ __forceinline__ bool photon_flight(const TransportArgs &A, const Smem &S, Lane &p, uint32_t &idx_out,
+                                              uint32_t &rz) {
     const PlanDev &P = S.plans[p.plan];
     const Phys &ph = A.phys;
     if (p.E < ph.p_cut_q) {
@@ -353,7 +358,7 @@ __device__ void photon_event(const TransportArgs &A, const Smem &S, Lane &p, int
             ledger_add(S, p.plan, 1, p.E);
         }
         p.act = false;
-        return;
+        return false;
     }
     const float xp = fmaf(__log2f((float)p.E), ph.grid.ph_a, ph.grid.ph_bq);
     const float mu_hat = interp_ldg(P.maj, xp);
@@ -365,7 +370,7 @@ __device__ void photon_event(const TransportArgs &A, const Smem &S, Lane &p, int
     if (!inside(P, p.x, p.y, p.z)) {
         ledger_add(S, p.plan, 1, p.E);
         p.act = false;
-        return;
+        return false;
     }
     int ix, iy, iz;
     const uint32_t idx = voxel_index(P, p.x, p.y, p.z, ix, iy, iz);
@@ -376,11 +381,28 @@ __device__ void photon_event(const TransportArgs &A, const Smem &S, Lane &p, int
     const bool pair_open = p.E > ph.two_mc2_q;
     float mu = rho * interp(tp, xp);
     if (!pair_open) mu = rho * (interp(tp + G, xp) + interp(tp + 2 * G, xp));
-    if (u01(r.y) * mu_hat > mu) return;  // fictitious: direction and energy unchanged
+    if (u01(r.y) * mu_hat > mu) return false;  // fictitious: direction and energy unchanged
     count(S, CNT_PH_REAL);
+    idx_out = idx;
+    rz = r.z;
+    return true;
+}
+
+__device__ __forceinline__ void photon_interact(const TransportArgs &A, const Smem &S, Lane &p, uint32_t idx,
+                                                uint32_t rz, int gw, int w) {
+    const PlanDev &P = S.plans[p.plan];
+    const Phys &ph = A.phys;
+    const float xp = fmaf(__log2f((float)p.E), ph.grid.ph_a, ph.grid.ph_bq);
+    const uint32_t vw = __ldg(P.vox + idx);
+    const int m = vw & (NMAT - 1);
+    const float rho = (float)(vw >> 4) * kRhoQ;
+    const float *tp = S.tab + TAB_PH + m * 3 * G;
+    const bool pair_open = p.E > ph.two_mc2_q;
+    float mu = rho * interp(tp, xp);
+    if (!pair_open) mu = rho * (interp(tp + G, xp) + interp(tp + 2 * G, xp));
     const float muC = rho * interp(tp + G, xp);
     const float mupe = rho * interp(tp + 2 * G, xp);
-    const float q = u01(r.z) * mu;
+    const float q = u01(rz) * mu;
     const float E = (float)p.E * kQf;
     if (q < muC) {
         // Compton scattering on a free electron (Klein-Nishina).
@@ -824,6 +846,9 @@ __device__ __forceinline__ void hard_pass(const TransportArgs &A, const Smem &S,
     __syncwarp();
 }
 
+// Woodcock flights a photon takes in one pass while its events are fictitious.
+constexpr int PH_FLIGHTS = 3;
+
 // ---------------------------------------------------------------------------
 // The kernel
 // ---------------------------------------------------------------------------
@@ -960,8 +985,21 @@ __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant_
         if (S.ws[w].stk[0] + 64u > A.stack_cap) spill_to_queue(A, S, gw, w, 0, 64u);
         if (S.ws[w].stk[1] + 64u > A.stack_cap) spill_to_queue(A, S, gw, w, 1, 64u);
         if (t == 0) {
-            if (lane == 0) atomicAdd(&S.cnt[CNT_PH_EVENTS], (unsigned long long)n_act);
-            if (p.act) photon_event(A, S, p, gw, w);
+            // Up to PH_FLIGHTS Woodcock flights per lane until its event is
+            // real, then the real events' interactions together: with many
+            // fictitious events (low densities under a high majorant) more
+            // lanes reach an interaction per pass; in a homogeneous medium
+            // every first flight is real and the loop ends at once.
+            uint32_t pidx = 0u, prz = 0u;
+            bool real = false;
+            for (int k = 0; k < PH_FLIGHTS; ++k) {
+                const bool fly = p.act && !real;
+                const unsigned flym = __ballot_sync(FULL, fly);
+                if (flym == 0u) break;
+                if (lane == 0) atomicAdd(&S.cnt[CNT_PH_EVENTS], (unsigned long long)__popc(flym));
+                if (fly) real = photon_flight(A, S, p, pidx, prz);
+            }
+            if (real) photon_interact(A, S, p, pidx, prz, gw, w);
         } else {
             uint32_t dep_idx = 0, dep_e = 0;
             bool stepped = false;
