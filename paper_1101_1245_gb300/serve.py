@@ -87,13 +87,14 @@ class Server:
     first_chunk   histories of a new plan's first round
     hbm_budget    bytes of tallies the server may hold at once
     rounds_in_flight  rounds on the device at once (1 .. MAX_INFLIGHT)
+    stagger_first     first checkpoints at 1, 2 or 3 first chunks by request id
     """
 
     def __init__(self, ctx: Context, hbm_budget: int, target: float = 0.01,
                  threshold: float = 0.5, n_batches: int = 16,
                  round_histories: int = 16_000_000, first_chunk: int = 200_000,
                  keep_dose: bool = False, clock: Callable[[], float] = time.perf_counter,
-                 rounds_in_flight: int = MAX_INFLIGHT):
+                 rounds_in_flight: int = MAX_INFLIGHT, stagger_first: bool = True):
         self.ctx = ctx
         self.budget = hbm_budget
         self.target = target
@@ -106,6 +107,7 @@ class Server:
         if not 1 <= rounds_in_flight <= MAX_INFLIGHT:
             raise ValueError(f"rounds_in_flight must be in [1, {MAX_INFLIGHT}]")
         self.depth = rounds_in_flight
+        self.stagger = stagger_first
         self.used = 0
         self.waiting: List[tuple] = []  # heap of (arrival, rid, request)
         self.active: Dict[int, _Active] = {}
@@ -157,7 +159,10 @@ class Server:
         point where its tally is next folded, within its share of the round."""
         q = self._quantum()
         if a.submitted == 0:
-            a.next_check = self.first_chunk
+            # first checkpoints at 1, 2 or 3 first chunks (by request id): requests
+            # that arrive together then reach their folds at different rounds, so
+            # the device is not idle while all of them fold at once
+            a.next_check = self.first_chunk * (1 + a.req.rid % 3 if self.stagger else 1)
         n = min(a.next_check - a.submitted, share)
         n = max(q, -(-n // q) * q)
         return int(max(1, min(n, a.req.max_histories - a.submitted)))
