@@ -158,3 +158,28 @@ def test_cached_blocks_yield_to_the_budget():
     assert used <= budget
     c.plan_close(p2)
     c.close()
+
+
+def test_launch_flags_select_compiled_kernels():
+    """The cycle profile and warp-aggregated deposits are separate kernel
+    instantiations (512 threads x 2 CTAs per SM): combining them, or asking
+    for more CTAs per SM, is rejected; each alone runs and gives the plain
+    kernel's tally."""
+    ctx = make_ctx()
+    with pytest.raises(g.GpumcdError) as e:
+        ctx.set_launch(flags=g.LAUNCH_PROFILE | g.LAUNCH_WARP_AGGREGATE)
+    assert e.value.status == g.ERR_INVALID_ARG
+    for flag in (g.LAUNCH_PROFILE, g.LAUNCH_WARP_AGGREGATE):
+        with pytest.raises(g.GpumcdError) as e:
+            ctx.set_launch(flags=flag, block_threads=256, blocks_per_sm=3)
+        assert e.value.status == g.ERR_INVALID_ARG
+    ph = W.homogeneous((24, 24, 24), 0.5, W.MAT_WATER, 1.0)
+    src = W.square_field(W.ELECTRON, 8.0, ph, 4.0)
+    doses = []
+    for flag in (0, g.LAUNCH_PROFILE, g.LAUNCH_WARP_AGGREGATE | g.LAUNCH_GRAPH):
+        ctx.set_launch(flags=flag, block_threads=512, blocks_per_sm=2)
+        pid = ctx.create_phantom(ph)
+        doses.append(ctx.simulate(pid, src, 20_000, 3, nvox=ph.nvox).dose)
+        ctx.destroy_phantom(pid)
+    assert all(np.array_equal(doses[0], d) for d in doses[1:])
+    ctx.close()
