@@ -94,7 +94,8 @@ class Server:
                  threshold: float = 0.5, n_batches: int = 16,
                  round_histories: int = 16_000_000, first_chunk: int = 200_000,
                  keep_dose: bool = False, clock: Callable[[], float] = time.perf_counter,
-                 rounds_in_flight: int = MAX_INFLIGHT, stagger_first: bool = True):
+                 rounds_in_flight: int = MAX_INFLIGHT, stagger_first: bool = True,
+                 log_rounds: bool = False):
         self.ctx = ctx
         self.budget = hbm_budget
         self.target = target
@@ -108,6 +109,8 @@ class Server:
             raise ValueError(f"rounds_in_flight must be in [1, {MAX_INFLIGHT}]")
         self.depth = rounds_in_flight
         self.stagger = stagger_first
+        # with log_rounds: (plans, histories, submitted_s, finished_s) per round
+        self.round_log: Optional[List[tuple]] = [] if log_rounds else None
         self.used = 0
         self.waiting: List[tuple] = []  # heap of (arrival, rid, request)
         self.active: Dict[int, _Active] = {}
@@ -117,7 +120,7 @@ class Server:
         self.max_active = 0
         self.max_used = 0
         self.folds = 0
-        self.inflight: collections.deque = collections.deque()  # (ticket, [(plan, histories)])
+        self.inflight: collections.deque = collections.deque()  # (ticket, [(plan, histories)], submitted_s)
         self.t0 = None
 
     # ---- requests ------------------------------------------------------
@@ -183,12 +186,14 @@ class Server:
             for a, n in zip(plans, chunks):
                 a.submitted += n
                 a.inflight += 1
-            self.inflight.append((ticket, list(zip(plans, chunks))))
+            self.inflight.append((ticket, list(zip(plans, chunks)), self._now()))
             self.rounds += 1
 
     def _finish_oldest(self) -> None:
-        ticket, pairs = self.inflight.popleft()
+        ticket, pairs, t_sub = self.inflight.popleft()
         self.ctx.wait(ticket)
+        if self.round_log is not None:
+            self.round_log.append((len(pairs), sum(n for _, n in pairs), t_sub, self._now()))
         for a, n in pairs:
             a.histories += n
             a.inflight -= 1
@@ -255,7 +260,7 @@ class Server:
                 self._fold_ready()
         finally:
             while self.inflight:  # leave no sequence in flight on an error
-                ticket, _ = self.inflight.popleft()
+                ticket = self.inflight.popleft()[0]
                 try:
                     self.ctx.wait(ticket)
                 except GpumcdError:
