@@ -948,8 +948,11 @@ __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant_
         // warp has few electrons left to step
         if (t == 1) {
             const unsigned hc = S.ws[w].hc;
-            // (n_act == 0 also when refill_low is 0: parked candidates must not be left behind)
-            if (hc >= 32u || (hc > 0u && (n_act == 0 || n_act < (int)A.refill_low))) {
+            // With few electrons left (the drain), a pass runs once the parked
+            // candidates outnumber the stepping electrons, not at every
+            // iteration; n_act == 0 keeps parked candidates from being left
+            // behind (also when refill_low is 0).
+            if (hc >= 32u || (hc > 0u && (n_act == 0 || (n_act < (int)A.refill_low && hc >= (unsigned)n_act)))) {
                 hard_pass(A, S, p, gw, w);
                 continue;
             }
