@@ -274,6 +274,17 @@ gpumcd_status gpumcd_plan_result_noalloc(gpumcd_ctx *ctx, int32_t plan_id, doubl
                                          gpumcd_run_stats *stats);
 
 /* ---- launch tuning ------------------------------------------------------ */
+
+/* Sets the launch of later runs; fields left 0 keep their value.  A new
+ * context starts at 512 threads x 2 CTAs per SM, stack_capacity 512,
+ * switch_high 320, refill_low 16, chunk 32, overflow_capacity 2^20, flags 0.
+ * Supported shapes are blocks_per_sm 1 or 2 with block_threads <= 512, and
+ * blocks_per_sm 3 or 4 with block_threads <= 256.  Also required:
+ * 128 <= stack_capacity <= 65536, 32 <= switch_high <= stack_capacity,
+ * refill_low <= 32, 1 <= chunk <= 4096 and 64 <= overflow_capacity <= 2^26.
+ * Anything else returns GPUMCD_ERR_INVALID_ARG, and so does a call while a
+ * submitted sequence is in flight (GPUMCD_ERR_STATE).  The launch changes the
+ * speed of a run, never its result. */
 gpumcd_status gpumcd_set_launch(gpumcd_ctx *ctx, const gpumcd_launch *launch);
 gpumcd_status gpumcd_get_launch(gpumcd_ctx *ctx, gpumcd_launch *launch);
 
