@@ -21,14 +21,14 @@ from typing import Optional
 # converged warp-instructions per transport event, electron beam / photon beam: the
 # physics of a step or photon event, measured on the kernel that ran each hard event
 # inline (no parking).  The kernel that parks hard-event candidates for converged
-# passes executes 22.0 / 19.6 per event (the parking is scheduling, not physics), so
+# passes executes 22.2 / 19.8 per event (the parking is scheduling, not physics), so
 # these are the algorithmic figures
 INST_PER_EVENT_E_BEAM: Optional[float] = 19.68
 INST_PER_EVENT_PH_BEAM: Optional[float] = 18.81
 # DRAM bytes (read + write) per transport launch of the benchmark step, from ncu on
-# the same workload at 1/5 of its histories, scaled by histories (787 MB electron
-# launch, 4.88 GB photon launch); None once the kernel has changed since the capture
-TRAFFIC_BYTES_PER_LAUNCH: Optional[float] = 2.83e9
+# the same workload at 1/5 of its histories, scaled by histories (790 MB electron
+# launch, 4.95 GB photon launch); None once the kernel has changed since the capture
+TRAFFIC_BYTES_PER_LAUNCH: Optional[float] = 2.87e9
 
 
 def alu_roofline(events_e_beam: int, events_ph_beam: int, kernel_ms: float, sm_mhz: Optional[float],
