@@ -317,6 +317,16 @@ gpumcd_status gpumcd_debug_sample(gpumcd_ctx *ctx, int32_t kind, double p0, int3
  * switches). */
 gpumcd_status gpumcd_debug_counters(gpumcd_ctx *ctx, uint64_t *out, int32_t *count);
 
+/* A phantom's majorant tables (GPUMCD §II.A mu_max, §II.B.3 electron
+ * Woodcock) and per-material maximum densities, copied to host arrays:
+ * majorants[0..511] = max over materials m of rho_max[m] * mu_m on the photon
+ * grid (1/cm), majorants[512..1023] = the running maximum over the electron
+ * grid of max_m rho_max[m] * Sigma_hard,m (1/cm); rho_max holds
+ * GPUMCD_MAX_MATERIALS entries (g/cm^3, 0 for materials absent from the
+ * phantom), each the largest density of that material after quantisation to
+ * 2^-24 g/cm^3.  Errors: GPUMCD_ERR_NOT_FOUND for an unknown phantom. */
+gpumcd_status gpumcd_debug_majorants(gpumcd_ctx *ctx, int32_t phantom, float *majorants, float *rho_max);
+
 /* Philox4x32-10 on the device: for i < n, out[4i..4i+3] = Philox(counter
  * ctr[4i..4i+3], key) (host arrays).  With use_curand != 0 the same words come
  * from cuRAND's Philox4_32_10 device generator started at that counter. */

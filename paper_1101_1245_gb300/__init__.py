@@ -130,6 +130,7 @@ SIGNATURES = {
     "gpumcd_debug_sample": (_ST, [_CTX, _I32, _D, _I32, C.POINTER(Source), _U64, _U64, _P]),
     "gpumcd_debug_counters": (_ST, [_CTX, _P, C.POINTER(_I32)]),
     "gpumcd_debug_philox": (_ST, [_CTX, _P, _P, _U64, _I32, _P]),
+    "gpumcd_debug_majorants": (_ST, [_CTX, _I32, _P, _P]),
 }
 
 _lock = threading.Lock()
@@ -398,6 +399,15 @@ class Context:
                          "cycles_per_iteration": cyc[i] / it[i] if it[i] else 0.0}
         out["refill_cycles"], out["switches"] = c[base + 6], c[base + 7]
         return out
+
+    def debug_majorants(self, phantom_id: int) -> Tuple[np.ndarray, np.ndarray]:
+        """The phantom's majorant tables (photon | electron, 1/cm, float32) and
+        per-material maximum densities (g/cm^3)."""
+        maj = np.zeros(1024, dtype=np.float32)
+        rho = np.zeros(MAX_MATERIALS, dtype=np.float32)
+        _check(self._L.gpumcd_debug_majorants(self.h, int(phantom_id), maj.ctypes.data, rho.ctypes.data),
+               "gpumcd_debug_majorants")
+        return maj, rho
 
     def debug_philox(self, ctr: np.ndarray, key: Sequence[int], use_curand: bool = False
                      ) -> np.ndarray:

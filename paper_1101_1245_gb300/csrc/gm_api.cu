@@ -1227,6 +1227,17 @@ gpumcd_status gpumcd_debug_counters(gpumcd_ctx *c, uint64_t *out, int32_t *count
     return GPUMCD_OK;
 }
 
+gpumcd_status gpumcd_debug_majorants(gpumcd_ctx *c, int32_t phantom, float *majorants, float *rho_max) {
+    if (!c || !majorants || !rho_max) return GPUMCD_ERR_INVALID_ARG;
+    auto it = c->phantoms.find(phantom);
+    if (it == c->phantoms.end()) return GPUMCD_ERR_NOT_FOUND;
+    ST(set_device(c));
+    CK(cudaMemcpyAsync(majorants, it->second.maj.p, MAJ_FLOATS * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(rho_max, it->second.rhomax.p, NMAT * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return GPUMCD_OK;
+}
+
 gpumcd_status gpumcd_debug_philox(gpumcd_ctx *c, const uint32_t *ctr, const uint32_t key[2], uint64_t n,
                                   int32_t use_curand, uint32_t *out) {
     if (!c || !ctr || !key || !out || n == 0 || n > (1ull << 24)) return GPUMCD_ERR_INVALID_ARG;

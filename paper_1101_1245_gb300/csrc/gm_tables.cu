@@ -227,15 +227,22 @@ __global__ void k_grid_energies(double p0, double p1, double e0, double e1, floa
 }
 
 // Voxel words: material id in bits 0-3, density in units of 2^-24 g/cm^3 in
-// bits 4-31.  rho_max per material via integer max of positive float bits.
+// bits 4-31.  rho_max per material via integer max of positive float bits:
+// reduced in the warp, then in the CTA's shared memory, then one global
+// atomic per material and CTA.
 __global__ void k_pack_phantom(const uint8_t *mat, const float *rho, uint64_t nvox, int n_mat,
                                uint32_t *vox, unsigned int *rho_max_bits, int *bad) {
+    __shared__ unsigned int smax[NMAT];
+    __shared__ int sbad;
+    for (int i = threadIdx.x; i < NMAT; i += blockDim.x) smax[i] = 0u;
+    if (threadIdx.x == 0) sbad = 0;
+    __syncthreads();
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < nvox;
          v += (uint64_t)gridDim.x * blockDim.x) {
         const int m = mat[v];
         const float r = rho[v];
         if (m >= n_mat || !(r > 0.f) || !(r < 16.f)) {
-            atomicExch(bad, 1);
+            sbad = 1;
             vox[v] = 0;
             continue;
         }
@@ -243,34 +250,49 @@ __global__ void k_pack_phantom(const uint8_t *mat, const float *rho, uint64_t nv
         if (rq == 0) rq = 1;
         if (rq >= (1u << 28)) rq = (1u << 28) - 1;
         vox[v] = (rq << 4) | (uint32_t)m;
-        // one atomic per distinct material in the warp
+        // one shared-memory atomic per distinct material in the warp
         const unsigned bits = __float_as_uint(__uint2float_rn(rq) * kRhoQ);
         const unsigned act = __activemask();
         const unsigned peers = __match_any_sync(act, m);
         const unsigned mx = __reduce_max_sync(peers, bits);
-        if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicMax(&rho_max_bits[m], mx);
+        if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicMax(&smax[m], mx);
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_mat && i < NMAT; i += blockDim.x)
+        if (smax[i]) atomicMax(&rho_max_bits[i], smax[i]);
+    if (threadIdx.x == 0 && sbad) atomicExch(bad, 1);
 }
 
 // Majorants of one phantom (GPUMCD §II.A mu_max; §II.B.3 electron Woodcock):
 // photon: max_m rho_max,m mu_m(E) per grid point; electron: running maximum
 // over the grid of max_m rho_max,m Sigma_hard,m(T), so that the value at T
 // bounds the hard cross-section at every energy an electron passes below T.
+// One thread per grid point (a block of G threads); the running maximum is an
+// inclusive prefix maximum, in the warp by shuffles and then across warps.
 __global__ void k_majorants(const float *tab, const unsigned int *rho_max_bits, int n_mat, float *maj) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    float run = 0.f;
-    for (int i = 0; i < G; ++i) {
-        float mp = 0.f, me = 0.f;
-        for (int m = 0; m < n_mat; ++m) {
-            const float r = __uint_as_float(rho_max_bits[m]);
-            if (r <= 0.f) continue;
-            mp = fmaxf(mp, r * tab[TAB_PH + (m * 3 + 0) * G + i]);
-            me = fmaxf(me, r * tab[TAB_EL + (m * 4 + 1) * G + i]);
-        }
-        run = fmaxf(run, me);
-        maj[i] = mp;
-        maj[G + i] = run;
+    __shared__ float wmax[G / 32];
+    const int i = threadIdx.x;
+    if (i >= G) return;
+    float mp = 0.f, me = 0.f;
+    for (int m = 0; m < n_mat; ++m) {
+        const float r = __uint_as_float(rho_max_bits[m]);
+        if (r <= 0.f) continue;
+        mp = fmaxf(mp, r * tab[TAB_PH + (m * 3 + 0) * G + i]);
+        me = fmaxf(me, r * tab[TAB_EL + (m * 4 + 1) * G + i]);
     }
+    maj[i] = mp;
+    const int lane = i & 31, w = i >> 5;
+    float run = me;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const float o = __shfl_up_sync(0xffffffffu, run, d);
+        if (lane >= d) run = fmaxf(run, o);
+    }
+    if (lane == 31) wmax[w] = run;
+    __syncthreads();
+    float base = 0.f;
+    for (int k = 0; k < w; ++k) base = fmaxf(base, wmax[k]);
+    maj[G + i] = fmaxf(base, run);
 }
 
 // Spectrum: FP64 prefix sum of the weights into a normalised CDF (the
@@ -514,14 +536,15 @@ cudaError_t launch_grid_energies(const TableGeom &g, float *out, cudaStream_t s)
 
 cudaError_t launch_pack_phantom(const uint8_t *mat, const float *rho, uint64_t nvox, int n_mat,
                                 uint32_t *vox, unsigned int *rho_max_bits, int *bad, cudaStream_t s) {
-    const int grid = (int)((nvox + 255) / 256 < 4096 ? (nvox + 255) / 256 : 4096);
+    const int grid = (int)((nvox + 255) / 256 < 1024 ? (nvox + 255) / 256 : 1024);
     k_pack_phantom<<<grid > 0 ? grid : 1, 256, 0, s>>>(mat, rho, nvox, n_mat, vox, rho_max_bits, bad);
     return cudaGetLastError();
 }
 
 cudaError_t launch_majorants(const float *tab, const unsigned int *rho_max_bits, int n_mat, float *maj,
                              cudaStream_t s) {
-    k_majorants<<<1, 32, 0, s>>>(tab, rho_max_bits, n_mat, maj);
+    static_assert(G % 32 == 0 && G <= 1024, "one thread per grid point in one block");
+    k_majorants<<<1, G, 0, s>>>(tab, rho_max_bits, n_mat, maj);
     return cudaGetLastError();
 }
 
