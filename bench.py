@@ -41,9 +41,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run each beam once at 1/5 of its histories (small case for ncu) and exit")
-    ap.add_argument("--workload", default="c2", choices=["c2", "batched", "served"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "batched", "served", "geoms", "ablation"],
                     help="c2: the contract line; batched: 64 uneven plans in one launch vs alone; "
-                         "served: a Poisson request stream with continuous batching")
+                         "served: a Poisson request stream with continuous batching; geoms: the "
+                         "paper's three geometries, each beam alone (Table resabsexec); ablation: "
+                         "the lane refill policies on the second geometry (Table resdivred)")
     ap.add_argument("--graph", action="store_true",
                     help="launch each sequence's first launch from a captured CUDA graph")
     ap.add_argument("--requests", type=int, default=1000, help="served: number of requests")
@@ -251,6 +253,34 @@ def run_ours(args):
     total_ms = max_over_ranks(sum(ms), dist, dev)
     value = (N_E + N_G) * args.steps * world / (total_ms / 1e3)
 
+    # the same step as one batched launch of both plans (the batched form on
+    # this workload; each plan's tally is bit-identical to its plain run)
+    def step_one_launch(i):
+        se = rank_seed(rank, i)
+        ctx.plan_reset(plan_e, se, sh)
+        ctx.plan_reset(plan_g, se + 1, sh)
+        ctx.run([plan_e, plan_g], [N_E, N_G], sh)
+        st_e = ctx.plan_result(plan_e, 0.5, out["de"].data_ptr(), out["se"].data_ptr(), sh)
+        st_g = ctx.plan_result(plan_g, 0.5, out["dg"].data_ptr(), out["sg"].data_ptr(), sh)
+        return st_e, st_g
+
+    for i in range(args.warmup):
+        step_one_launch(-1 - i)
+    ev1 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    st1 = None
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            ev1[i][0].record(stream)
+            st1 = step_one_launch(i)
+            ev1[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms1 = sum(a.elapsed_time(b) for a, b in ev1) / args.steps
+    one_launch = {"value": (N_E + N_G) * world / (ms1 / 1e3), "ms_per_step": ms1,
+                  "over_plain": (total_ms / args.steps) / ms1, "transport_ms": st1[0]["transport_ms"]}
+
     # end to end through the C ABI with host buffers: each step uploads the
     # phantom from pinned host memory, runs both beams through gpumcd_simulate
     # and reads dose and sigma back into pinned host memory
@@ -308,7 +338,8 @@ def run_ours(args):
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "host_memory": "pinned"},
             "gpu_launches": launches,
-            "clocks": clocks}
+            "clocks": clocks,
+            "batched_one_launch": one_launch}
     if cpu:
         line["cpu_baseline"] = {"value": cpu[0], "unit": UNIT, "cores": cpu[1], "kind": "oracle",
                                 "sample": cpu[2]}
@@ -402,6 +433,135 @@ def run_batched(args):
           "autotuned_launch": tuned["launch"], "autotune_trials": len(tuned["trials"]),
           "n_batches": 16, "steps": args.steps, "launch_graph": bool(args.graph), "data": "synthetic"})
     ctx.close()
+
+
+# GPUMCD Table "resabsexec" (GTX480, seconds for 1e6 electrons / 4e6 photons at
+# 15 MeV), quoted beside the GB300 times as context only
+PAPER_ABSEXEC_S = {("geom1", "electron"): 0.118, ("geom2", "electron"): 0.147, ("geom3", "electron"): 0.162,
+                   ("geom1", "photon"): 0.269, ("geom2", "photon"): 0.275, ("geom3", "photon"): 0.366}
+
+
+def run_geoms(args):
+    """The paper's three geometries (GPUMCD §III.A) with its timing beams: the
+    water phantom (the c2 workload), the lung box and the tissue / lung / bone
+    slabs, each beam run alone from a zeroed tally to FP64 dose and sigma.
+    Also reports the share of fictitious events, which the bone slab's
+    majorant drives up."""
+    import torch
+
+    import paper_1101_1245_gb300 as g
+    import workloads as W
+
+    ctx = g.engine(0, mats=W.MATERIALS_PAPER)
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    rows = []
+    for geom, make in (("geom1", W.config2), ("geom2", W.geom2), ("geom3", W.geom3)):
+        for particle in (W.ELECTRON, W.PHOTON):
+            pl = make(particle)
+            pid = ctx.create_phantom(pl.phantom)
+            plan = ctx.plan_open(pid, pl.source, pl.seed, 32)
+
+            def once(seed):
+                ctx.plan_reset(plan, seed)
+                torch.cuda.synchronize()
+                ev[0].record()
+                ctx.run([plan], [pl.n_histories])
+                st = ctx.plan_result(plan, 0.5)
+                ev[1].record()
+                torch.cuda.synchronize()
+                return ev[0].elapsed_time(ev[1]), st
+
+            for i in range(max(1, args.warmup)):
+                once(1000 + i)
+            res = [once(2000 + i) for i in range(args.steps)]
+            ms = statistics.median(r[0] for r in res)
+            st = res[-1][1]
+            name = "electron" if particle == W.ELECTRON else "photon"
+            ph_ev = st["n_photon_events"]
+            hard = st["n_hard_real"] + st["n_hard_fict"]
+            rows.append({"geometry": geom, "beam": name, "histories": pl.n_histories, "ms": ms,
+                         "transport_ms": statistics.median(r[1]["transport_ms"] for r in res),
+                         "histories_per_s": pl.n_histories / (ms / 1e3),
+                         "paper_gtx480_s": PAPER_ABSEXEC_S[(geom, name)],
+                         "photon_fictitious_share": (ph_ev - st["n_photon_real"]) / ph_ev if ph_ev else 0.0,
+                         "hard_fictitious_share": st["n_hard_fict"] / hard if hard else 0.0,
+                         "electron_steps_per_history": st["n_electron_steps"] / pl.n_histories,
+                         "ledger_exact": st["e_deposited"] + st["e_escaped"] + st["e_rest"] == st["e_incident"]})
+            ctx.plan_close(plan)
+            ctx.destroy_phantom(pid)
+    ctx.close()
+    emit({"workload": "paper_geometries_15MeV", "metric": "ms per beam (1e6 e- or 4e6 photons, to FP64 dose + sigma)",
+          "unit": "ms", "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
+          "phantoms": "128^3 at 0.25 cm: water; lung box in water; tissue/lung/bone slabs",
+          "data": "synthetic", "rows": rows})
+
+
+# GPUMCD Table "resdivred" (GTX480, geometry 2): base time in seconds and the
+# accelerations of stream compaction and of the persistent pool, as context
+PAPER_DIVRED = {"electron": {"t_base_s": 0.185, "a_comp": 1.06, "a_pool": 1.26},
+                "photon": {"t_base_s": 0.275, "a_comp": 0.85, "a_pool": 0.98}}
+
+
+def run_ablation(args):
+    """Divergence-reduction ablation (GPUMCD §II.C.3, Table resdivred) on the
+    paper's second geometry with its timing beams: the lane refill policies of
+    the persistent kernel.  base = a warp's lanes refill only when all are
+    empty; comp N = every N-th pass (the paper's compaction after N steps);
+    pool = every pass (the production policy).  Tallies are identical under
+    every policy, which the line checks."""
+    import hashlib
+
+    import torch
+
+    import paper_1101_1245_gb300 as g
+    import workloads as W
+
+    ctx = g.engine(0)
+    policies = [("base", g.REFILL_WHEN_EMPTY), ("comp64", 64), ("comp16", 16), ("comp4", 4), ("pool", 1)]
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    rows = []
+    for particle in (W.ELECTRON, W.PHOTON):
+        pl = W.geom2(particle)
+        pid = ctx.create_phantom(pl.phantom)
+        plan = ctx.plan_open(pid, pl.source, pl.seed, 32)
+        d = torch.zeros(pl.phantom.nvox, dtype=torch.float64, device="cuda")
+        sg = torch.zeros_like(d)
+        name = "electron" if particle == W.ELECTRON else "photon"
+        times, hashes = {}, set()
+        for label, period in policies:
+            ctx.set_launch(refill_period=period)
+
+            def once(seed):
+                ctx.plan_reset(plan, seed)
+                torch.cuda.synchronize()
+                ev[0].record()
+                ctx.run([plan], [pl.n_histories])
+                st = ctx.plan_result(plan, 0.5, d.data_ptr(), sg.data_ptr())
+                ev[1].record()
+                torch.cuda.synchronize()
+                return ev[0].elapsed_time(ev[1]), st["transport_ms"]
+
+            for i in range(max(1, args.warmup)):
+                once(pl.seed)
+            res = [once(pl.seed) for _ in range(args.steps)]
+            hashes.add(hashlib.sha256(d.cpu().numpy().tobytes() + sg.cpu().numpy().tobytes()).hexdigest())
+            times[label] = (statistics.median(r[0] for r in res), statistics.median(r[1] for r in res))
+        ctx.set_launch(refill_period=1)
+        tb = times["base"][1]
+        rows.append({"beam": name, "histories": pl.n_histories,
+                     "transport_ms": {k: v[1] for k, v in times.items()},
+                     "step_ms": {k: v[0] for k, v in times.items()},
+                     "a_comp": {k: tb / times[k][1] for k in ("comp64", "comp16", "comp4")},
+                     "a_pool": tb / times["pool"][1],
+                     "tallies_identical": len(hashes) == 1,
+                     "paper_gtx480": PAPER_DIVRED[name]})
+        ctx.plan_close(plan)
+        ctx.destroy_phantom(pid)
+    ctx.close()
+    emit({"workload": "ablation_refill_policy_geom2_15MeV",
+          "metric": "transport ms per beam under each lane refill policy; A = T_base / T",
+          "unit": "ms", "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
+          "phantom": "lung box in water, 128^3 at 0.25 cm", "data": "synthetic", "rows": rows})
 
 
 def run_served(args):
@@ -504,6 +664,12 @@ def main():
         return
     if args.workload == "served":
         run_served(args)
+        return
+    if args.workload == "geoms":
+        run_geoms(args)
+        return
+    if args.workload == "ablation":
+        run_ablation(args)
         return
     if args.impl == "reference":
         run_reference(args)

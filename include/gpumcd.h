@@ -104,7 +104,22 @@ typedef struct {
     uint32_t chunk;           /* primaries or queued particles a warp claims at once */
     uint32_t overflow_capacity; /* global overflow queue entries per type */
     uint32_t flags;           /* GPUMCD_LAUNCH_* */
+    uint32_t refill_period;   /* lane refill policy, the divergence-reduction ablation (below) */
 } gpumcd_launch;
+
+/* refill_period: 1 (the default) refills a warp's empty lanes at every pass,
+ * the persistent "pool" of GPUMCD §II.C.3.  N >= 2 refills them only every
+ * N-th pass of the warp or when all its lanes are empty, like the paper's
+ * stream compaction after N steps.  GPUMCD_REFILL_WHEN_EMPTY refills only
+ * an empty warp, so each set of 32 particles runs until its slowest one ends
+ * (the paper's base configuration).  In the last two forms a warp also
+ * considers a low-occupancy type switch only on refill passes.  Hard-event
+ * passes and type switches by stack level stay on in every form.  The
+ * tallies do not depend on the form.  A form other than 1 runs a separately
+ * compiled kernel: it needs blocks_per_sm <= 2 and neither
+ * GPUMCD_LAUNCH_PROFILE nor GPUMCD_LAUNCH_WARP_AGGREGATE (else
+ * GPUMCD_ERR_INVALID_ARG). */
+#define GPUMCD_REFILL_WHEN_EMPTY 0xFFFFFFFFu
 
 #define GPUMCD_LAUNCH_WARP_AGGREGATE 1u /* combine a warp's deposits to one voxel into one atomic */
 #define GPUMCD_LAUNCH_PROFILE 2u        /* count clock cycles per event type (see gpumcd_debug_counters) */

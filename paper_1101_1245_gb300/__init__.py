@@ -29,6 +29,8 @@ BEAM_PENCIL, BEAM_SQUARE = 0, 1
 LAUNCH_WARP_AGGREGATE = 1
 LAUNCH_PROFILE = 2
 LAUNCH_GRAPH = 4
+# refill_period of the launch: refill empty lanes only when the whole warp is empty
+REFILL_WHEN_EMPTY = 0xFFFFFFFF
 PARTICLE_TYPES = ("photon", "electron")
 
 STATUS = {
@@ -69,7 +71,8 @@ class Launch(C.Structure):
     _fields_ = [("block_threads", C.c_uint32), ("blocks_per_sm", C.c_uint32),
                 ("stack_capacity", C.c_uint32), ("switch_high", C.c_uint32),
                 ("refill_low", C.c_uint32), ("chunk", C.c_uint32),
-                ("overflow_capacity", C.c_uint32), ("flags", C.c_uint32)]
+                ("overflow_capacity", C.c_uint32), ("flags", C.c_uint32),
+                ("refill_period", C.c_uint32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

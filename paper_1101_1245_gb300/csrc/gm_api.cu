@@ -335,6 +335,7 @@ gpumcd_status gpumcd_init(gpumcd_ctx **out, int32_t device, uint64_t hbm_budget_
     c->launch.chunk = 32;
     c->launch.overflow_capacity = 1u << 20;
     c->launch.flags = 0;
+    c->launch.refill_period = 1;
     *out = c;
     return GPUMCD_OK;
 }
@@ -826,6 +827,7 @@ gpumcd_status seq_start(gpumcd_ctx *c, Slot &sl, int32_t n_plans, const int32_t 
     A.stack_cap = c->launch.stack_capacity;
     A.switch_high = c->launch.switch_high;
     A.refill_low = c->launch.refill_low;
+    A.refill_period = c->launch.refill_period;
     A.chunk = c->launch.chunk;
     A.flags = c->launch.flags;
     A.counters = dc->counters;
@@ -1128,6 +1130,7 @@ gpumcd_status gpumcd_set_launch(gpumcd_ctx *c, const gpumcd_launch *l) {
     if (l->chunk) n.chunk = l->chunk;
     if (l->overflow_capacity) n.overflow_capacity = l->overflow_capacity;
     n.flags = l->flags;
+    if (l->refill_period) n.refill_period = l->refill_period;
     if (n.block_threads % 32 || n.block_threads < 32 || n.block_threads > 512) return GPUMCD_ERR_INVALID_ARG;
     if (n.blocks_per_sm < 1 || n.blocks_per_sm > 4) return GPUMCD_ERR_INVALID_ARG;
     // supported (threads, CTAs/SM) pairs follow the kernel's launch-bound variants
@@ -1144,6 +1147,10 @@ gpumcd_status gpumcd_set_launch(gpumcd_ctx *c, const gpumcd_launch *l) {
     if ((n.flags & (GPUMCD_LAUNCH_PROFILE | GPUMCD_LAUNCH_WARP_AGGREGATE)) && n.blocks_per_sm > 2)
         return GPUMCD_ERR_INVALID_ARG;
     if ((n.flags & GPUMCD_LAUNCH_PROFILE) && (n.flags & GPUMCD_LAUNCH_WARP_AGGREGATE)) return GPUMCD_ERR_INVALID_ARG;
+    // the refill-policy ablation kernel: 512 threads x 2 CTAs per SM at most, alone
+    if (n.refill_period != 1u &&
+        (n.blocks_per_sm > 2 || (n.flags & (GPUMCD_LAUNCH_PROFILE | GPUMCD_LAUNCH_WARP_AGGREGATE))))
+        return GPUMCD_ERR_INVALID_ARG;
     c->launch = n;
     return GPUMCD_OK;
 }

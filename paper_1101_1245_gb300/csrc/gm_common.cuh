@@ -126,6 +126,7 @@ struct TransportArgs {
     HardRec *hard;                     // [warp][HARD_CAP] parked hard-event candidates
     uint32_t stack_cap, switch_high, refill_low, chunk;
     uint32_t flags;
+    uint32_t refill_period;            // 1: refill every pass; N: every N-th pass or when empty
     unsigned long long *counters;      // run counters (see CNT_*)
     int32_t *error;                    // device status word
 };

@@ -856,10 +856,11 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// PROF compiles in the per-type cycle profile (GPUMCD_LAUNCH_PROFILE) and AGG
-// the warp-aggregated deposit (GPUMCD_LAUNCH_WARP_AGGREGATE); the production
-// instantiations carry neither.
-template <int MAXT, int MINB, bool PROF, bool AGG>
+// PROF compiles in the per-type cycle profile (GPUMCD_LAUNCH_PROFILE), AGG
+// the warp-aggregated deposit (GPUMCD_LAUNCH_WARP_AGGREGATE) and SCHED the
+// refill policies of the divergence-reduction ablation (refill_period != 1);
+// the production instantiations carry none of them.
+template <int MAXT, int MINB, bool PROF, bool AGG, bool SCHED>
 __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant__ TransportArgs A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *tab = (float *)smem_raw;
@@ -940,7 +941,21 @@ __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant_
             }
         }
         long long c0 = prof ? clock64() : 0;
-        const int n_act = refill(A, S, F, p, gw, w, t);
+        int n_act;
+        bool fresh = true;  // this pass refilled the lanes
+        if (SCHED && A.refill_period != 1u) {
+            // the ablation's refill policies (GPUMCD §II.C.3): empty lanes wait
+            // for every N-th pass, or for the whole warp to empty
+            const unsigned actm = __ballot_sync(FULL, p.act);
+            if (actm != 0u && (A.refill_period == 0xFFFFFFFFu || iter % A.refill_period != 0u)) {
+                n_act = __popc(actm);
+                fresh = false;
+            } else {
+                n_act = refill(A, S, F, p, gw, w, t);
+            }
+        } else {
+            n_act = refill(A, S, F, p, gw, w, t);
+        }
         if (prof && lane == 0) atomicAdd(&S.cnt[CNT_PROF_REFILL_CYC], (unsigned long long)(clock64() - c0));
         const int o = 1 - t;
         // electrons: a converged hard pass once 32 candidates are parked (a
@@ -966,7 +981,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant_
         }
         const unsigned so = S.ws[w].stk[o], st = S.ws[w].stk[t];
         if ((so >= A.switch_high && so > st + 32u) ||
-            (n_act < (int)A.refill_low && available(A, S, F, w, o) >= 32u)) {
+            (n_act < (int)A.refill_low && fresh && available(A, S, F, w, o) >= 32u)) {
             if (prof && lane == 0) atomicAdd(&S.cnt[CNT_PROF_SWITCHES], 1ull);
             // switch type: park the current particles on their stack
             if (S.ws[w].stk[t] + 32u > A.stack_cap) spill_to_queue(A, S, gw, w, t, 64u);
@@ -1041,22 +1056,24 @@ size_t transport_smem_bytes(int /*block_threads*/) {
 typedef void (*TransportKernel)(const TransportArgs);
 struct Variant {
     int max_threads, min_blocks;
-    bool prof, agg;
+    bool prof, agg, sched;
     TransportKernel fn;
 };
 static const Variant kVariants[] = {
-    {512, 1, false, false, k_transport<512, 1, false, false>},
-    {384, 2, false, false, k_transport<384, 2, false, false>},
-    {512, 2, false, false, k_transport<512, 2, false, false>},
-    {256, 3, false, false, k_transport<256, 3, false, false>},
-    {256, 4, false, false, k_transport<256, 4, false, false>},
-    {512, 2, true, false, k_transport<512, 2, true, false>},
-    {512, 2, false, true, k_transport<512, 2, false, true>},
+    {512, 1, false, false, false, k_transport<512, 1, false, false, false>},
+    {384, 2, false, false, false, k_transport<384, 2, false, false, false>},
+    {512, 2, false, false, false, k_transport<512, 2, false, false, false>},
+    {256, 3, false, false, false, k_transport<256, 3, false, false, false>},
+    {256, 4, false, false, false, k_transport<256, 4, false, false, false>},
+    {512, 2, true, false, false, k_transport<512, 2, true, false, false>},
+    {512, 2, false, true, false, k_transport<512, 2, false, true, false>},
+    {512, 2, false, false, true, k_transport<512, 2, false, false, true>},
 };
 
-static TransportKernel pick_variant(int block, int blocks_per_sm, bool prof, bool agg) {
+static TransportKernel pick_variant(int block, int blocks_per_sm, bool prof, bool agg, bool sched) {
     for (const Variant &v : kVariants)
-        if (v.prof == prof && v.agg == agg && block <= v.max_threads && blocks_per_sm <= v.min_blocks)
+        if (v.prof == prof && v.agg == agg && v.sched == sched && block <= v.max_threads &&
+            blocks_per_sm <= v.min_blocks)
             return v.fn;
     return nullptr;
 }
@@ -1072,7 +1089,7 @@ cudaError_t transport_configure(int block_threads) {
 
 cudaError_t launch_transport(const TransportArgs &a, int grid, int block, int blocks_per_sm, cudaStream_t s) {
     TransportKernel fn = pick_variant(block, blocks_per_sm, (a.flags & GPUMCD_LAUNCH_PROFILE) != 0u,
-                                      (a.flags & GPUMCD_LAUNCH_WARP_AGGREGATE) != 0u);
+                                      (a.flags & GPUMCD_LAUNCH_WARP_AGGREGATE) != 0u, a.refill_period != 1u);
     if (!fn) return cudaErrorInvalidConfiguration;
     fn<<<grid, block, transport_smem_bytes(block), s>>>(a);
     return cudaGetLastError();

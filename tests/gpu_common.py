@@ -32,8 +32,8 @@ def run_gpu(ctx, plan, n=None, seed=None):
     return r
 
 
-def run_oracle(plan, n=None, seed=None, flags=0):
-    return oracle.simulate(W.MATERIALS, W.DEFAULT_PHYSICS, plan.phantom, plan.source,
+def run_oracle(plan, n=None, seed=None, flags=0, mats=None):
+    return oracle.simulate(mats if mats is not None else W.MATERIALS, W.DEFAULT_PHYSICS, plan.phantom, plan.source,
                            n or plan.n_histories, plan.seed if seed is None else seed, flags,
                            processes=host_cores())
 

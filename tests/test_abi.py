@@ -64,3 +64,31 @@ def test_binding_constants_match_the_header():
                         ("ERR_BUDGET", g.ERR_BUDGET), ("ERR_STATE", g.ERR_STATE)):
         assert defs["GPUMCD_" + name] == value, name
         assert g.status_string(value) == g.STATUS[value]
+
+
+def test_refill_when_empty_matches_the_header():
+    text = open(HEADER).read()
+    m = re.search(r"^#define GPUMCD_REFILL_WHEN_EMPTY (0x[0-9A-Fa-f]+)u", text, flags=re.M)
+    assert m and int(m.group(1), 16) == g.REFILL_WHEN_EMPTY
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """sizeof and field offsets of the ABI structs, from a C compiler reading
+    the header, equal those of the binding's ctypes structures."""
+    structs = {"gpumcd_launch": g.Launch, "gpumcd_run_stats": g.RunStats}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "gpumcd.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for cname, cls in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)

@@ -160,6 +160,24 @@ def test_cached_blocks_yield_to_the_budget():
     c.close()
 
 
+def test_refill_policy_validation():
+    """A refill policy other than every pass runs its own kernel, compiled for
+    up to 512 threads x 2 CTAs per SM and without the profile or the
+    warp-aggregated deposits."""
+    ctx = make_ctx()
+    for bad in (dict(refill_period=4, block_threads=256, blocks_per_sm=3),
+                dict(refill_period=g.REFILL_WHEN_EMPTY, flags=g.LAUNCH_PROFILE),
+                dict(refill_period=16, flags=g.LAUNCH_WARP_AGGREGATE)):
+        with pytest.raises(g.GpumcdError) as e:
+            ctx.set_launch(**bad)
+        assert e.value.status == g.ERR_INVALID_ARG
+    ctx.set_launch(refill_period=8, flags=g.LAUNCH_GRAPH)
+    assert ctx.get_launch()["refill_period"] == 8
+    ctx.set_launch(refill_period=1, flags=0)
+    assert ctx.get_launch()["refill_period"] == 1
+    ctx.close()
+
+
 def test_launch_flags_select_compiled_kernels():
     """The cycle profile and warp-aggregated deposits are separate kernel
     instantiations (512 threads x 2 CTAs per SM): combining them, or asking

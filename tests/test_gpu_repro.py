@@ -32,6 +32,12 @@ def _dose(ctx, ph, src, n, seed, splits=(None,)):
     return d.cpu().numpy(), s.cpu().numpy(), st
 
 
+# the ledger and every event counter that depends only on the particles'
+# histories (not on scheduling: launches, spills and overflows do)
+EVENT_KEYS = ("e_incident", "e_deposited", "e_escaped", "e_rest", "n_photon_events", "n_photon_real",
+              "n_compton", "n_photo", "n_pair", "n_electron_steps", "n_hard_real", "n_hard_fict",
+              "n_moller", "n_brem", "n_photons", "n_electrons", "n_sampler_capped")
+
 SOURCES = {
     "electron": W.Source(W.ELECTRON, W.BEAM_SQUARE, energy=12.0, center_cm=(6.0, 5.0), field_cm=4.0),
     "photon": W.Source(W.PHOTON, W.BEAM_SQUARE, energy=15.0, center_cm=(6.0, 5.0), field_cm=4.0),
@@ -57,6 +63,10 @@ def reference():
     dict(flags=g.LAUNCH_PROFILE),
     dict(flags=g.LAUNCH_GRAPH),
     dict(stack_capacity=128, switch_high=64, overflow_capacity=1 << 16, chunk=256),
+    # the refill policies of the divergence-reduction ablation (their own kernel)
+    dict(refill_period=4),
+    dict(refill_period=16),
+    dict(refill_period=g.REFILL_WHEN_EMPTY),
 ])
 def test_bit_identical_across_launch_shapes(reference, kind, launch):
     ph, out = reference
@@ -66,10 +76,12 @@ def test_bit_identical_across_launch_shapes(reference, kind, launch):
     d0, s0, st0 = out[kind]
     assert np.array_equal(d, d0)
     assert np.array_equal(s, s0)
-    for k in ("e_incident", "e_deposited", "e_escaped", "e_rest", "n_electron_steps",
-              "n_photon_events", "n_hard_real"):
+    for k in EVENT_KEYS:
         assert st[k] == st0[k], k
     assert st["e_deposited"] + st["e_escaped"] + st["e_rest"] == st["e_incident"]
+    # every real photon event is one interaction, every real hard event one of two
+    assert st["n_compton"] + st["n_photo"] + st["n_pair"] == st["n_photon_real"]
+    assert st["n_moller"] + st["n_brem"] == st["n_hard_real"]
 
 
 @pytest.mark.parametrize("kind", ["electron", "photon"])

@@ -6,10 +6,32 @@ import workloads as W
 
 
 def test_materials_fractions():
-    for m in W.MATERIALS:
+    for m in W.MATERIALS_PAPER:
         assert sum(m.w) == pytest.approx(1.0, abs=1e-12)
         assert len(m.Z) <= W.MAX_ELEMENTS
     assert W.WATER.w[0] == pytest.approx(0.1119, abs=2e-4)
+
+
+def test_paper_geometries():
+    """GPUMCD §III.A: the lung box (electrons 4 cm from 3 cm depth, photons
+    6.5 cm from 5.5 cm; 4.5 cm wide, on the axis) and the tissue / lung /
+    bone slabs (2/2/2 cm and 3/2/7 cm), on 128^3 at 0.25 cm."""
+    assert W.MATERIALS_PAPER[:3] == W.MATERIALS and W.MATERIALS_PAPER[W.MAT_TISSUE].name == "tissue"
+    for particle, (z0, z1) in ((W.ELECTRON, (12, 28)), (W.PHOTON, (22, 48))):
+        ph = W.geom2(particle).phantom
+        col = ph.mat[:, 64, 64]
+        assert (col[z0:z1] == W.MAT_LUNG).all() and (col[:z0] == W.MAT_WATER).all()
+        assert (col[z1:] == W.MAT_WATER).all()
+        row = ph.mat[(z0 + z1) // 2, 64, :]
+        assert int((row == W.MAT_LUNG).sum()) == 18  # 4.5 cm
+        assert np.allclose(ph.rho[ph.mat == W.MAT_LUNG], 0.26)
+    for particle, cuts in ((W.ELECTRON, (8, 16, 24)), (W.PHOTON, (12, 20, 48))):
+        ph = W.geom3(particle).phantom
+        col = ph.mat[:, 10, 100]
+        a, b, c = cuts
+        assert (col[:a] == W.MAT_TISSUE).all() and (col[a:b] == W.MAT_LUNG).all()
+        assert (col[b:c] == W.MAT_BONE).all() and (col[c:] == W.MAT_TISSUE).all()
+        assert np.allclose(ph.rho[:, 10, 100][b:c], 1.85)
 
 
 def test_config3_slabs():

@@ -80,6 +80,13 @@ BONE = Material(
 
 MATERIALS: Tuple[Material, ...] = (WATER, LUNG, BONE)
 MAT_WATER, MAT_LUNG, MAT_BONE = 0, 1, 2
+# Soft tissue for the paper's third geometry (GPUMCD §III.A), which names the
+# material but not its data: the ICRU four-component soft tissue (mass
+# fractions H 0.101, C 0.111, N 0.026, O 0.762; I = 74.9 eV; 1.0 g/cm^3).
+TISSUE = Material("tissue", (("H", 0.101), ("C", 0.111), ("N", 0.026), ("O", 0.762)), 74.9, 1.0)
+# The material set of the paper's geometries: the three above plus tissue.
+MATERIALS_PAPER: Tuple[Material, ...] = (WATER, LUNG, BONE, TISSUE)
+MAT_TISSUE = 3
 
 
 @dataclasses.dataclass(frozen=True)
@@ -270,6 +277,41 @@ def config2(particle: int, n_histories: Optional[int] = None, n: int = 128,
     if particle == ELECTRON:
         return Plan("c2_water128_15MeV_electron", ph, src, n_histories or 1_000_000, 1)
     return Plan("c2_water128_15MeV_photon", ph, src, n_histories or 4_000_000, 2)
+
+
+def geom2(particle: int, n_histories: Optional[int] = None, n: int = 128,
+          voxel_cm: float = 0.25) -> Plan:
+    """The paper's second geometry (GPUMCD §III.A): a lung box (0.26 g/cm^3) in
+    water, centred on the beam axis, 4.5 cm wide; for electrons 4 cm long from
+    a depth of 3 cm, for photons 6.5 cm long from 5.5 cm.  The timing-case
+    beams: 15 MeV, 10x10 cm^2, 1e6 electrons (seed 1) or 4e6 photons (seed 2).
+    Materials: MATERIALS."""
+    X = n * voxel_cm
+    z0, dz = (3.0, 4.0) if particle == ELECTRON else (5.5, 6.5)
+    lo = (X / 2 - 2.25, X / 2 - 2.25, z0)
+    hi = (X / 2 + 2.25, X / 2 + 2.25, z0 + dz)
+    ph = box_in_water((n, n, n), voxel_cm, lo, hi, MAT_LUNG, 0.26)
+    src = square_field(particle, 15.0, ph, 10.0)
+    name = f"geom2_lungbox{n}_15MeV_" + ("electron" if particle == ELECTRON else "photon")
+    return Plan(name, ph, src, n_histories or (1_000_000 if particle == ELECTRON else 4_000_000),
+                1 if particle == ELECTRON else 2)
+
+
+def geom3(particle: int, n_histories: Optional[int] = None, n: int = 128,
+          voxel_cm: float = 0.25) -> Plan:
+    """The paper's third geometry (GPUMCD §III.A): slabs along the beam of soft
+    tissue, lung (0.26) and bone (1.85); for electrons 2 / 2 / 2 cm then
+    tissue, for photons 3 / 2 / 7 cm then tissue.  Beams as in geom2.
+    Materials: MATERIALS_PAPER (tissue is material 3)."""
+    if particle == ELECTRON:
+        slabs = [(2.0, MAT_TISSUE, 1.0), (2.0, MAT_LUNG, 0.26), (2.0, MAT_BONE, 1.85), (1e9, MAT_TISSUE, 1.0)]
+    else:
+        slabs = [(3.0, MAT_TISSUE, 1.0), (2.0, MAT_LUNG, 0.26), (7.0, MAT_BONE, 1.85), (1e9, MAT_TISSUE, 1.0)]
+    ph = z_slabs((n, n, n), voxel_cm, slabs)
+    src = square_field(particle, 15.0, ph, 10.0)
+    name = f"geom3_tissue_lung_bone{n}_15MeV_" + ("electron" if particle == ELECTRON else "photon")
+    return Plan(name, ph, src, n_histories or (1_000_000 if particle == ELECTRON else 4_000_000),
+                1 if particle == ELECTRON else 2)
 
 
 def config3(n_histories: int = 10_000_000, n: int = 256, voxel_cm: float = 0.2,
