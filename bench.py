@@ -41,11 +41,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run each beam once at 1/5 of its histories (small case for ncu) and exit")
-    ap.add_argument("--workload", default="c2", choices=["c2", "batched", "served", "geoms", "ablation"],
+    ap.add_argument("--workload", default="c2",
+                    choices=["c2", "batched", "served", "geoms", "ablation", "kerma"],
                     help="c2: the contract line; batched: 64 uneven plans in one launch vs alone; "
                          "served: a Poisson request stream with continuous batching; geoms: the "
                          "paper's three geometries, each beam alone (Table resabsexec); ablation: "
-                         "the lane refill policies on the second geometry (Table resdivred)")
+                         "the lane refill policies on the second geometry (Table resdivred); "
+                         "kerma: the photon-only mode against full transport on the c2 photon beam")
     ap.add_argument("--graph", action="store_true",
                     help="launch each sequence's first launch from a captured CUDA graph")
     ap.add_argument("--requests", type=int, default=1000, help="served: number of requests")
@@ -564,6 +566,68 @@ def run_ablation(args):
           "phantom": "lung box in water, 128^3 at 0.25 cm", "data": "synthetic", "rows": rows})
 
 
+def run_kerma(args):
+    """The photon-only mode (GPUMCD_LAUNCH_KERMA) against full coupled
+    transport on the c2 photon beam (15 MeV, 4e6 photons, 128^3 water): time,
+    and the central-axis depth dose of each (mean over the central 1x1 cm)."""
+    import numpy as np
+    import torch
+
+    import paper_1101_1245_gb300 as g
+    import workloads as W
+
+    ctx = g.engine(0)
+    pl = W.config2(W.PHOTON)
+    ph = pl.phantom
+    pid = ctx.create_phantom(ph)
+    plan = ctx.plan_open(pid, pl.source, pl.seed, 32)
+    d = torch.zeros(ph.nvox, dtype=torch.float64, device="cuda")
+    sg = torch.zeros_like(d)
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    nx, ny, nz = ph.dims
+    h = 2  # central 1x1 cm at 0.25 cm voxels
+    out = {}
+    for label, flags in (("transport", 0), ("kerma", g.LAUNCH_KERMA)):
+        ctx.set_launch(flags=flags)
+
+        def once():
+            ctx.plan_reset(plan, pl.seed)
+            torch.cuda.synchronize()
+            ev[0].record()
+            ctx.run([plan], [pl.n_histories])
+            st = ctx.plan_result(plan, 0.5, d.data_ptr(), sg.data_ptr())
+            ev[1].record()
+            torch.cuda.synchronize()
+            return ev[0].elapsed_time(ev[1]), st
+
+        for _ in range(max(1, args.warmup)):
+            once()
+        res = [once() for _ in range(args.steps)]
+        dose = d.cpu().numpy().reshape(nz, ny, nx)
+        pdd = dose[:, ny // 2 - h:ny // 2 + h, nx // 2 - h:nx // 2 + h].mean(axis=(1, 2))
+        st = res[-1][1]
+        out[label] = {"ms": statistics.median(r[0] for r in res),
+                      "transport_ms": statistics.median(r[1]["transport_ms"] for r in res),
+                      "electron_steps": st["n_electron_steps"], "pdd": pdd}
+    ctx.set_launch(flags=0)
+    ctx.close()
+    t, k = out["transport"], out["kerma"]
+    depths = [0.125, 1.125, 3.125, 5.125, 10.125, 20.125]  # voxel centres, cm
+    norm = t["pdd"].max()
+    emit({"workload": "c2_photon_kerma_vs_transport", "metric": "ms per beam and central-axis dose",
+          "unit": "ms", "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
+          "histories": pl.n_histories, "data": "synthetic",
+          "transport_ms": t["transport_ms"], "kerma_ms": k["transport_ms"],
+          "speedup": t["transport_ms"] / k["transport_ms"],
+          "step_ms": {"transport": t["ms"], "kerma": k["ms"]},
+          "electron_steps": {"transport": t["electron_steps"], "kerma": k["electron_steps"]},
+          "depth_of_max_cm": {"transport": float(np.argmax(t["pdd"]) * 0.25 + 0.125),
+                              "kerma": float(np.argmax(k["pdd"]) * 0.25 + 0.125)},
+          "pdd_over_transport_max": {f"{z:g}": {"transport": float(t["pdd"][int(z / 0.25)] / norm),
+                                                "kerma": float(k["pdd"][int(z / 0.25)] / norm)}
+                                     for z in depths}})
+
+
 def run_served(args):
     """Config 5: a Poisson stream of dose requests from the config-4
     distribution on resident phantoms, served with continuous batching to a
@@ -670,6 +734,9 @@ def main():
         return
     if args.workload == "ablation":
         run_ablation(args)
+        return
+    if args.workload == "kerma":
+        run_kerma(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -116,16 +116,23 @@ typedef struct {
  * considers a low-occupancy type switch only on refill passes.  Hard-event
  * passes and type switches by stack level stay on in every form.  The
  * tallies do not depend on the form.  A form other than 1 runs a separately
- * compiled kernel: it needs blocks_per_sm <= 2 and neither
- * GPUMCD_LAUNCH_PROFILE nor GPUMCD_LAUNCH_WARP_AGGREGATE (else
- * GPUMCD_ERR_INVALID_ARG). */
+ * compiled kernel: it needs blocks_per_sm <= 2 and none of GPUMCD_LAUNCH_PROFILE,
+ * GPUMCD_LAUNCH_WARP_AGGREGATE or GPUMCD_LAUNCH_KERMA (else GPUMCD_ERR_INVALID_ARG). */
 #define GPUMCD_REFILL_WHEN_EMPTY 0xFFFFFFFFu
 
 #define GPUMCD_LAUNCH_WARP_AGGREGATE 1u /* combine a warp's deposits to one voxel into one atomic */
 #define GPUMCD_LAUNCH_PROFILE 2u        /* count clock cycles per event type (see gpumcd_debug_counters) */
 /* The two flags above select separately compiled kernels: each needs blocks_per_sm <= 2, and
- * they cannot be combined (GPUMCD_ERR_INVALID_ARG). */
+ * they cannot be combined with each other, with GPUMCD_LAUNCH_KERMA or with a refill_period
+ * other than 1 (GPUMCD_ERR_INVALID_ARG). */
 #define GPUMCD_LAUNCH_GRAPH 4u          /* replay a sequence's first launch from a captured CUDA graph */
+/* Photon-only transport: every electron (a photon's secondary, or a primary) deposits its
+ * kinetic energy in the voxel where it is created, and no electron is transported.  The
+ * "photon-only fast mode" of the paper's outlook; the dose is then the kerma of the photon
+ * field (kinetic energy released per mass), not the absorbed dose.  A separately compiled
+ * kernel: it needs blocks_per_sm <= 2 and none of GPUMCD_LAUNCH_PROFILE,
+ * GPUMCD_LAUNCH_WARP_AGGREGATE or a refill_period other than 1 (else GPUMCD_ERR_INVALID_ARG). */
+#define GPUMCD_LAUNCH_KERMA 8u
 
 /* Counters of one run.  The ledger satisfies, exactly,
  * e_deposited + e_escaped + e_rest == e_incident. */

@@ -29,6 +29,7 @@ BEAM_PENCIL, BEAM_SQUARE = 0, 1
 LAUNCH_WARP_AGGREGATE = 1
 LAUNCH_PROFILE = 2
 LAUNCH_GRAPH = 4
+LAUNCH_KERMA = 8
 # refill_period of the launch: refill empty lanes only when the whole warp is empty
 REFILL_WHEN_EMPTY = 0xFFFFFFFF
 PARTICLE_TYPES = ("photon", "electron")

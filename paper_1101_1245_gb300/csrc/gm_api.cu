@@ -1147,10 +1147,11 @@ gpumcd_status gpumcd_set_launch(gpumcd_ctx *c, const gpumcd_launch *l) {
     if ((n.flags & (GPUMCD_LAUNCH_PROFILE | GPUMCD_LAUNCH_WARP_AGGREGATE)) && n.blocks_per_sm > 2)
         return GPUMCD_ERR_INVALID_ARG;
     if ((n.flags & GPUMCD_LAUNCH_PROFILE) && (n.flags & GPUMCD_LAUNCH_WARP_AGGREGATE)) return GPUMCD_ERR_INVALID_ARG;
-    // the refill-policy ablation kernel: 512 threads x 2 CTAs per SM at most, alone
-    if (n.refill_period != 1u &&
-        (n.blocks_per_sm > 2 || (n.flags & (GPUMCD_LAUNCH_PROFILE | GPUMCD_LAUNCH_WARP_AGGREGATE))))
-        return GPUMCD_ERR_INVALID_ARG;
+    // the refill-policy ablation kernel and the photon-only kernel: 512 threads
+    // x 2 CTAs per SM at most, each alone
+    const int special = ((n.flags & GPUMCD_LAUNCH_PROFILE) != 0u) + ((n.flags & GPUMCD_LAUNCH_WARP_AGGREGATE) != 0u) +
+                        (n.refill_period != 1u) + ((n.flags & GPUMCD_LAUNCH_KERMA) != 0u);
+    if (special > 1 || (special == 1 && n.blocks_per_sm > 2)) return GPUMCD_ERR_INVALID_ARG;
     c->launch = n;
     return GPUMCD_OK;
 }

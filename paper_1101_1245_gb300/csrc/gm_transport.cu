@@ -176,6 +176,19 @@ __device__ __forceinline__ void push(const TransportArgs &A, const Smem &S, int 
     count(S, type == 0 ? CNT_PHOTONS : CNT_ELECTRONS);
 }
 
+// An electron set in motion by a photon: pushed for transport, or, in the
+// photon-only mode (GPUMCD_LAUNCH_KERMA), deposited in the voxel `idx` of the
+// photon's interaction.
+template <bool KERMA>
+__device__ __forceinline__ void emit_electron(const TransportArgs &A, const Smem &S, int gw, int w,
+                                              const PlanDev &P, uint32_t idx, float vx, float vy, float vz,
+                                              uint32_t E, const Lane &parent, uint32_t j) {
+    if (KERMA)
+        deposit(P, parent.hist, idx, E);
+    else
+        push(A, S, gw, w, 1, parent.x, parent.y, parent.z, vx, vy, vz, E, parent, j);
+}
+
 __device__ __forceinline__ void load_rec(Lane &p, const Rec &r) {
     const float4 a = r.a;
     const float4 b = r.b;
@@ -388,6 +401,7 @@ __device__ __forceinline__ bool photon_flight(const TransportArgs &A, const Smem
     return true;
 }
 
+template <bool KERMA>
 __device__ __forceinline__ void photon_interact(const TransportArgs &A, const Smem &S, Lane &p, uint32_t idx,
                                                 uint32_t rz, int gw, int w) {
     const PlanDev &P = S.plans[p.plan];
@@ -424,7 +438,7 @@ __device__ __forceinline__ void photon_interact(const TransportArgs &A, const Sm
             const float e1f = (float)e1 * kQf;
             float ex = E * p.ux - e1f * vx, ey = E * p.uy - e1f * vy, ez = E * p.uz - e1f * vz;
             const float n = rsqrtf(fmaxf(ex * ex + ey * ey + ez * ez, 1e-30f));
-            push(A, S, gw, w, 1, p.x, p.y, p.z, ex * n, ey * n, ez * n, te, p, 0);
+            emit_electron<KERMA>(A, S, gw, w, P, idx, ex * n, ey * n, ez * n, te, p, 0);
         } else {
             deposit(P, p.hist, idx, te);
         }
@@ -449,7 +463,7 @@ __device__ __forceinline__ void photon_interact(const TransportArgs &A, const Sm
             const float sn = sqrtf(fmaxf(0.0f, (1.0f - c) * (1.0f + c)));
             float vx = p.ux, vy = p.uy, vz = p.uz;
             rotate(vx, vy, vz, c, sn, cp, sp);
-            push(A, S, gw, w, 1, p.x, p.y, p.z, vx, vy, vz, p.E, p, 0);
+            emit_electron<KERMA>(A, S, gw, w, P, idx, vx, vy, vz, p.E, p, 0);
         } else {
             deposit(P, p.hist, idx, p.E);
         }
@@ -474,7 +488,7 @@ __device__ __forceinline__ void photon_interact(const TransportArgs &A, const Sm
                 __sincosf(th, &st, &ct);
                 float vx = p.ux, vy = p.uy, vz = p.uz;
                 rotate(vx, vy, vz, ct, st, j == 0 ? cp : -cp, j == 0 ? sp : -sp);
-                push(A, S, gw, w, 1, p.x, p.y, p.z, vx, vy, vz, te, p, (uint32_t)j);
+                emit_electron<KERMA>(A, S, gw, w, P, idx, vx, vy, vz, te, p, (uint32_t)j);
             } else {
                 deposit(P, p.hist, idx, te);
             }
@@ -700,6 +714,7 @@ __device__ void spill_to_queue(const TransportArgs &A, const Smem &S, int gw, in
 
 // Fill empty lanes with particles of type t.  Returns the number of lanes
 // that hold a particle afterwards.
+template <bool KERMA>
 __device__ int refill(const TransportArgs &A, const Smem &S, CtaFlags &F, Lane &p, int gw, int w, int t) {
     const int lane = threadIdx.x & 31;
     WarpState &ws = S.ws[w];
@@ -771,6 +786,16 @@ __device__ int refill(const TransportArgs &A, const Smem &S, CtaFlags &F, Lane &
             const uint32_t plan = A.prim_plan[t][a];
             const PlanDev &P = S.plans[plan];
             ledger_add(S, plan, 0, make_primary(p, P, plan, P.hist_base + (g - A.prim_off[t][a])));
+            if (KERMA && t == 1) {
+                // photon-only mode: a primary electron deposits where it enters
+                if (inside(P, p.x, p.y, p.z)) {
+                    int ix, iy, iz;
+                    deposit(P, p.hist, voxel_index(P, p.x, p.y, p.z, ix, iy, iz), p.E);
+                } else {
+                    ledger_add(S, plan, 1, p.E);
+                }
+                p.act = false;
+            }
         }
         __syncwarp();
         if (lane == 0) {
@@ -857,10 +882,11 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
 }
 
 // PROF compiles in the per-type cycle profile (GPUMCD_LAUNCH_PROFILE), AGG
-// the warp-aggregated deposit (GPUMCD_LAUNCH_WARP_AGGREGATE) and SCHED the
-// refill policies of the divergence-reduction ablation (refill_period != 1);
-// the production instantiations carry none of them.
-template <int MAXT, int MINB, bool PROF, bool AGG, bool SCHED>
+// the warp-aggregated deposit (GPUMCD_LAUNCH_WARP_AGGREGATE), SCHED the
+// refill policies of the divergence-reduction ablation (refill_period != 1)
+// and KERMA the photon-only mode (GPUMCD_LAUNCH_KERMA); the production
+// instantiations carry none of them.
+template <int MAXT, int MINB, bool PROF, bool AGG, bool SCHED, bool KERMA>
 __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant__ TransportArgs A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *tab = (float *)smem_raw;
@@ -951,10 +977,10 @@ __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant_
                 n_act = __popc(actm);
                 fresh = false;
             } else {
-                n_act = refill(A, S, F, p, gw, w, t);
+                n_act = refill<KERMA>(A, S, F, p, gw, w, t);
             }
         } else {
-            n_act = refill(A, S, F, p, gw, w, t);
+            n_act = refill<KERMA>(A, S, F, p, gw, w, t);
         }
         if (prof && lane == 0) atomicAdd(&S.cnt[CNT_PROF_REFILL_CYC], (unsigned long long)(clock64() - c0));
         const int o = 1 - t;
@@ -1017,7 +1043,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant_
                 if (lane == 0) atomicAdd(&S.cnt[CNT_PH_EVENTS], (unsigned long long)__popc(flym));
                 if (fly) real = photon_flight(A, S, p, pidx, prz);
             }
-            if (real) photon_interact(A, S, p, pidx, prz, gw, w);
+            if (real) photon_interact<KERMA>(A, S, p, pidx, prz, gw, w);
         } else {
             uint32_t dep_idx = 0, dep_e = 0;
             bool stepped = false;
@@ -1056,23 +1082,24 @@ size_t transport_smem_bytes(int /*block_threads*/) {
 typedef void (*TransportKernel)(const TransportArgs);
 struct Variant {
     int max_threads, min_blocks;
-    bool prof, agg, sched;
+    bool prof, agg, sched, kerma;
     TransportKernel fn;
 };
 static const Variant kVariants[] = {
-    {512, 1, false, false, false, k_transport<512, 1, false, false, false>},
-    {384, 2, false, false, false, k_transport<384, 2, false, false, false>},
-    {512, 2, false, false, false, k_transport<512, 2, false, false, false>},
-    {256, 3, false, false, false, k_transport<256, 3, false, false, false>},
-    {256, 4, false, false, false, k_transport<256, 4, false, false, false>},
-    {512, 2, true, false, false, k_transport<512, 2, true, false, false>},
-    {512, 2, false, true, false, k_transport<512, 2, false, true, false>},
-    {512, 2, false, false, true, k_transport<512, 2, false, false, true>},
+    {512, 1, false, false, false, false, k_transport<512, 1, false, false, false, false>},
+    {384, 2, false, false, false, false, k_transport<384, 2, false, false, false, false>},
+    {512, 2, false, false, false, false, k_transport<512, 2, false, false, false, false>},
+    {256, 3, false, false, false, false, k_transport<256, 3, false, false, false, false>},
+    {256, 4, false, false, false, false, k_transport<256, 4, false, false, false, false>},
+    {512, 2, true, false, false, false, k_transport<512, 2, true, false, false, false>},
+    {512, 2, false, true, false, false, k_transport<512, 2, false, true, false, false>},
+    {512, 2, false, false, true, false, k_transport<512, 2, false, false, true, false>},
+    {512, 2, false, false, false, true, k_transport<512, 2, false, false, false, true>},
 };
 
-static TransportKernel pick_variant(int block, int blocks_per_sm, bool prof, bool agg, bool sched) {
+static TransportKernel pick_variant(int block, int blocks_per_sm, bool prof, bool agg, bool sched, bool kerma) {
     for (const Variant &v : kVariants)
-        if (v.prof == prof && v.agg == agg && v.sched == sched && block <= v.max_threads &&
+        if (v.prof == prof && v.agg == agg && v.sched == sched && v.kerma == kerma && block <= v.max_threads &&
             blocks_per_sm <= v.min_blocks)
             return v.fn;
     return nullptr;
@@ -1089,7 +1116,8 @@ cudaError_t transport_configure(int block_threads) {
 
 cudaError_t launch_transport(const TransportArgs &a, int grid, int block, int blocks_per_sm, cudaStream_t s) {
     TransportKernel fn = pick_variant(block, blocks_per_sm, (a.flags & GPUMCD_LAUNCH_PROFILE) != 0u,
-                                      (a.flags & GPUMCD_LAUNCH_WARP_AGGREGATE) != 0u, a.refill_period != 1u);
+                                      (a.flags & GPUMCD_LAUNCH_WARP_AGGREGATE) != 0u, a.refill_period != 1u,
+                                      (a.flags & GPUMCD_LAUNCH_KERMA) != 0u);
     if (!fn) return cudaErrorInvalidConfiguration;
     fn<<<grid, block, transport_smem_bytes(block), s>>>(a);
     return cudaGetLastError();

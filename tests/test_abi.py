@@ -58,6 +58,8 @@ def test_binding_constants_match_the_header():
     defs = {k: int(v) for k, v in re.findall(r"^#define (GPUMCD_\w+) \(?(-?\d+)u?\)?", text, flags=re.M)}
     assert defs["GPUMCD_MAX_PLANS_PER_RUN"] == g.MAX_PLANS_PER_RUN
     assert defs["GPUMCD_MAX_INFLIGHT"] == g.MAX_INFLIGHT
+    for name in ("LAUNCH_WARP_AGGREGATE", "LAUNCH_PROFILE", "LAUNCH_GRAPH", "LAUNCH_KERMA"):
+        assert defs["GPUMCD_" + name] == getattr(g, name), name
     for name, value in (("OK", g.OK), ("ERR_INVALID_ARG", g.ERR_INVALID_ARG), ("ERR_OOM", g.ERR_OOM),
                         ("ERR_CUDA", g.ERR_CUDA), ("ERR_QUEUE_OVERFLOW", g.ERR_QUEUE_OVERFLOW),
                         ("ERR_TIMEOUT", g.ERR_TIMEOUT), ("ERR_NOT_FOUND", g.ERR_NOT_FOUND),

@@ -161,13 +161,16 @@ def test_cached_blocks_yield_to_the_budget():
 
 
 def test_refill_policy_validation():
-    """A refill policy other than every pass runs its own kernel, compiled for
-    up to 512 threads x 2 CTAs per SM and without the profile or the
-    warp-aggregated deposits."""
+    """A refill policy other than every pass, and the photon-only mode, each run
+    their own kernel, compiled for up to 512 threads x 2 CTAs per SM and alone
+    (without the profile, the warp-aggregated deposits or each other)."""
     ctx = make_ctx()
     for bad in (dict(refill_period=4, block_threads=256, blocks_per_sm=3),
                 dict(refill_period=g.REFILL_WHEN_EMPTY, flags=g.LAUNCH_PROFILE),
-                dict(refill_period=16, flags=g.LAUNCH_WARP_AGGREGATE)):
+                dict(refill_period=16, flags=g.LAUNCH_WARP_AGGREGATE),
+                dict(refill_period=4, flags=g.LAUNCH_KERMA),
+                dict(flags=g.LAUNCH_KERMA | g.LAUNCH_PROFILE),
+                dict(flags=g.LAUNCH_KERMA, block_threads=256, blocks_per_sm=3)):
         with pytest.raises(g.GpumcdError) as e:
             ctx.set_launch(**bad)
         assert e.value.status == g.ERR_INVALID_ARG

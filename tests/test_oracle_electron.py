@@ -81,6 +81,27 @@ def test_brem_hard_plus_soft_equals_total_radiative(mat, T):
     assert oracle.xs("sigma_brem", mat, T, kc) == pytest.approx(hard_n, rel=1e-9)
 
 
+@pytest.mark.parametrize("mat", [W.WATER, W.BONE, W.TISSUE])
+def test_hard_cross_section_rises_with_energy(mat):
+    """The electron Woodcock test of GPUMCD §II.B.3 takes its majorant at the
+    energy of the step's start.  That is exact only where the hard
+    cross-section (Moller above 2 T_c plus bremsstrahlung above k_c) does not
+    fall as the energy falls along the step. In this model it rises
+    monotonically from the cut-off to 20 MeV in every material. So the
+    paper's step-start majorant equals the envelope majorant, the running
+    maximum over lower energies, that the oracle and the GPU tabulate. The
+    paper-literal variant is thus the same model.  The grid is finer than the
+    GPU's 512-point table."""
+    P = W.DEFAULT_PHYSICS
+    T = np.geomspace(P.e_abs, P.e_max, 4001)
+    sig = np.array([oracle.xs("sigma_moller", mat, t, P.t_c) + oracle.xs("sigma_brem", mat, t, P.k_c)
+                    for t in T])
+    assert np.all(np.diff(sig) >= 0.0)
+    assert np.array_equal(np.maximum.accumulate(sig), sig)
+    # Moller opens at 2 T_c: zero below, positive above
+    assert oracle.xs("sigma_moller", mat, 0.39, P.t_c) == 0.0 < oracle.xs("sigma_moller", mat, 0.41, P.t_c)
+
+
 def test_brem_log_growth_small_cut():
     """For k_c << T the hard cross-section grows like (4/3)(S_A + S_1/12) ln(T/k_c)."""
     T = 10.0
