@@ -457,7 +457,8 @@ def run_geoms(args):
     ctx = g.engine(0, mats=W.MATERIALS_PAPER)
     ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     rows = []
-    for geom, make in (("geom1", W.config2), ("geom2", W.geom2), ("geom3", W.geom3)):
+    for geom, make in (("geom1", W.config2), ("geom2", W.geom2), ("geom3", W.geom3),
+                       ("synthetic_ct", W.synthetic_ct)):
         for particle in (W.ELECTRON, W.PHOTON):
             pl = make(particle)
             pid = ctx.create_phantom(pl.phantom)
@@ -484,7 +485,7 @@ def run_geoms(args):
             rows.append({"geometry": geom, "beam": name, "histories": pl.n_histories, "ms": ms,
                          "transport_ms": statistics.median(r[1]["transport_ms"] for r in res),
                          "histories_per_s": pl.n_histories / (ms / 1e3),
-                         "paper_gtx480_s": PAPER_ABSEXEC_S[(geom, name)],
+                         "paper_gtx480_s": PAPER_ABSEXEC_S.get((geom, name)),
                          "photon_fictitious_share": (ph_ev - st["n_photon_real"]) / ph_ev if ph_ev else 0.0,
                          "hard_fictitious_share": st["n_hard_fict"] / hard if hard else 0.0,
                          "electron_steps_per_history": st["n_electron_steps"] / pl.n_histories,
@@ -494,7 +495,8 @@ def run_geoms(args):
     ctx.close()
     emit({"workload": "paper_geometries_15MeV", "metric": "ms per beam (1e6 e- or 4e6 photons, to FP64 dose + sigma)",
           "unit": "ms", "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
-          "phantoms": "128^3 at 0.25 cm: water; lung box in water; tissue/lung/bone slabs",
+          "phantoms": "128^3 at 0.25 cm: water; lung box in water; tissue/lung/bone slabs; "
+                      "synthetic-CT thorax 128x96x128 (6 MV-like photons, 15 MeV electrons)",
           "data": "synthetic", "rows": rows})
 
 

@@ -105,6 +105,30 @@ __device__ __forceinline__ uint32_t voxel_index(const PlanDev &P, float x, float
     return (uint32_t)ix + (uint32_t)P.nx * ((uint32_t)iy + (uint32_t)P.ny * (uint32_t)iz);
 }
 
+// A particle left exactly on a voxel face it is moving out through (its
+// distance to the exit is 0) is moved to the voxel it enters: face_step gives
+// the index change along one axis, +-1 when the coordinate lies within 4 FP32
+// ulps (in voxel units) of the face ahead of it in the direction of motion.
+// In FP32 a step that ends a nudge beyond a face at a grazing angle can round
+// back onto the face; indexed by position alone the particle would then stay
+// in the voxel it is leaving and creep on in nudge-sized steps (seen in thin
+// air, where nothing deflects it).
+__device__ __forceinline__ int face_step(float x, float inv_d, float u, int i) {
+    const float f = x * inv_d;
+    const float fr = f - (float)i;
+    const float eps = fmaxf(f, 1.0f) * (1.0f / 2097152.0f);  // 2^-21: 4 ulps of f
+    return (u < 0.f && fr < eps) ? -1 : ((u > 0.f && fr > 1.0f - eps) ? 1 : 0);
+}
+
+// Distance along the direction to the exit face of voxel (ix, iy, iz).
+__device__ __forceinline__ float exit_distance(const PlanDev &P, const Lane &p, int ix, int iy, int iz) {
+    float dv = 3.0e38f;
+    if (p.ux != 0.f) dv = fminf(dv, ((p.ux > 0.f ? (float)(ix + 1) : (float)ix) - p.x * P.inv_dx) * P.dx / p.ux);
+    if (p.uy != 0.f) dv = fminf(dv, ((p.uy > 0.f ? (float)(iy + 1) : (float)iy) - p.y * P.inv_dy) * P.dy / p.uy);
+    if (p.uz != 0.f) dv = fminf(dv, ((p.uz > 0.f ? (float)(iz + 1) : (float)iz) - p.z * P.inv_dz) * P.dz / p.uz);
+    return dv;
+}
+
 // Fire-and-forget 64-bit add into the tally (no value comes back).
 __device__ __forceinline__ void red_add_u64(unsigned long long *addr, unsigned long long v) {
     asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(addr), "l"(v) : "memory");
@@ -311,7 +335,9 @@ __device__ __forceinline__ float ms_mu(const float *tab, const Grid &gr, float g
     if (g1 < (float)MS_G_MIN) return 0.0f;
     if (g1 > (float)MS_G_MAX) return z;
     const float a = __expf(interp_ms(tab + TAB_MS, fmaf(__log2f(g1), gr.ms_a, gr.ms_b)));
-    return a * z / (1.0f + a - z);
+    // at z = 1 the exact value is 1; in FP32, 1 + a rounds to 1 when a < 2^-24
+    // and the quotient would be a / 0
+    return fminf(a * z / (1.0f + a - z), 1.0f);
 }
 
 __device__ __forceinline__ float sample_spectrum(const PlanDev &P, float z) {
@@ -513,8 +539,33 @@ __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, in
         return false;
     }
     int ix, iy, iz;
-    const uint32_t idx0 = voxel_index(P, p.x, p.y, p.z, ix, iy, iz);
-    const uint32_t vw = __ldg(P.vox + idx0);
+    uint32_t idx0 = voxel_index(P, p.x, p.y, p.z, ix, iy, iz);
+    uint32_t vw = __ldg(P.vox + idx0);
+    // distance to the voxel faces along u
+    float dv = exit_distance(P, p, ix, iy, iz);
+    if (dv <= 0.0f && p.draw >= 2u) {
+        // on the face it is leaving: FP32 rounded the last step's end back onto
+        // the face it crossed, and the particle belongs to the voxel it enters.
+        // A particle's first steps (draw counter below 2) keep the voxel of its
+        // position, so one created exactly on a face takes a nudge-length step
+        // across it first, as in FP64.
+        const int sx = face_step(p.x, P.inv_dx, p.ux, ix), sy = face_step(p.y, P.inv_dy, p.uy, iy),
+                  sz = face_step(p.z, P.inv_dz, p.uz, iz);
+        if (sx | sy | sz) {
+            ix += sx;
+            iy += sy;
+            iz += sz;
+            if ((unsigned)ix >= (unsigned)P.nx || (unsigned)iy >= (unsigned)P.ny || (unsigned)iz >= (unsigned)P.nz) {
+                ledger_add(S, p.plan, 1, p.E);
+                p.act = false;
+                return false;
+            }
+            idx0 = (uint32_t)ix + (uint32_t)P.nx * ((uint32_t)iy + (uint32_t)P.ny * (uint32_t)iz);
+            vw = __ldg(P.vox + idx0);
+            dv = exit_distance(P, p, ix, iy, iz);
+        }
+    }
+    dv = fmaxf(dv, 0.0f) + ph.nudge;
     const int m0 = vw & (NMAT - 1);
     const float rho0 = (float)(vw >> 4) * kRhoQ;
     if (p.E < ph.e_abs_q) {
@@ -527,12 +578,6 @@ __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, in
     const float xe = fmaf(__log2f((float)p.E), ph.grid.el_a, ph.grid.el_bq);
     const float L0 = rho0 * interp(te, xe);
     const float smax = ph.estepe * T / L0;
-    // distance to the voxel faces along u, plus the nudge
-    float dv = 3.0e38f;
-    if (p.ux != 0.f) dv = fminf(dv, ((p.ux > 0.f ? (float)(ix + 1) : (float)ix) - p.x * P.inv_dx) * P.dx / p.ux);
-    if (p.uy != 0.f) dv = fminf(dv, ((p.uy > 0.f ? (float)(iy + 1) : (float)iy) - p.y * P.inv_dy) * P.dy / p.uy);
-    if (p.uz != 0.f) dv = fminf(dv, ((p.uz > 0.f ? (float)(iz + 1) : (float)iz) - p.z * P.inv_dz) * P.dz / p.uz);
-    dv = fmaxf(dv, 0.0f) + ph.nudge;
     const float sig_hat = interp_ldg(P.maj + G, xe);
     const uint4 r = draw4(p, P);
     const float ehard = -__logf(u01(r.x)) / sig_hat;
@@ -569,7 +614,8 @@ __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, in
         p.act = false;
         return true;
     }
-    const uint32_t idx1 = voxel_index(P, p.x, p.y, p.z, ix, iy, iz);
+    int jx, jy, jz;
+    const uint32_t idx1 = voxel_index(P, p.x, p.y, p.z, jx, jy, jz);
     if (e1 < ph.e_abs_q) {
         deposit(P, p.hist, idx1, e1);
         p.act = false;

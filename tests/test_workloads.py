@@ -34,6 +34,33 @@ def test_paper_geometries():
         assert np.allclose(ph.rho[:, 10, 100][b:c], 1.85)
 
 
+def test_hu_calibration_and_thresholds():
+    """The HU -> density curve passes through its points, is monotone, and the
+    material follows the HU thresholds."""
+    hu = np.array([-1000.0, -740.0, -400.0, -1.0, 0.0, 249.0, 250.0, 1400.0, 3000.0, 5000.0]).reshape(1, 1, -1)
+    ph = W.hu_to_phantom(hu, 0.5)
+    rho, mat = ph.rho.ravel(), ph.mat.ravel()
+    assert rho[0] == np.float32(0.0012) and rho[1] == np.float32(0.26) and rho[4] == np.float32(1.0)
+    assert rho[7] == np.float32(1.85) and rho[8] == np.float32(2.8) and rho[9] == np.float32(2.8)
+    assert np.all(np.diff(rho) >= 0)
+    assert list(mat) == [W.MAT_LUNG, W.MAT_LUNG, W.MAT_TISSUE, W.MAT_TISSUE, W.MAT_TISSUE, W.MAT_TISSUE,
+                         W.MAT_BONE, W.MAT_BONE, W.MAT_BONE, W.MAT_BONE]
+
+
+def test_synthetic_ct_is_seeded_and_thorax_like():
+    a = W.synthetic_ct_hu((40, 8, 40), 0.5, 6)
+    b = W.synthetic_ct_hu((40, 8, 40), 0.5, 6)
+    c = W.synthetic_ct_hu((40, 8, 40), 0.5, 7)
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    ph = W.synthetic_ct(W.PHOTON, dims=(64, 16, 64), voxel_cm=0.5).phantom
+    frac = {m: float((ph.mat == m).mean()) for m in (W.MAT_LUNG, W.MAT_BONE, W.MAT_TISSUE)}
+    assert 0.3 < frac[W.MAT_TISSUE] < 0.5 and 0.005 < frac[W.MAT_BONE] < 0.05
+    assert ph.rho.min() == np.float32(0.0012) and 1.6 < ph.rho.max() < 1.9
+    # the beam axis crosses tissue, the sternum and a lung-free mediastinum
+    col = ph.mat[:, 8, 32]
+    assert W.MAT_BONE in col and W.MAT_TISSUE in col
+
+
 def test_config3_slabs():
     pl = W.config3(n=256, voxel_cm=0.2)
     ph = pl.phantom

@@ -314,6 +314,74 @@ def geom3(particle: int, n_histories: Optional[int] = None, n: int = 128,
                 1 if particle == ELECTRON else 2)
 
 
+# ---------------------------------------------------------------------------
+# Synthetic CT (the paper's outlook, §V, names CT-derived phantoms; no CT data
+# is available, so a seeded HU volume stands in for one)
+# ---------------------------------------------------------------------------
+# HU -> density calibration, piecewise linear through (HU, g/cm^3) points: air,
+# lung, water, then a bone branch reaching cortical bone at 1400 HU
+HU_CALIBRATION = ((-1000.0, 0.0012), (-740.0, 0.26), (0.0, 1.0), (1400.0, 1.85), (3000.0, 2.8))
+HU_LUNG_BELOW = -400.0  # material by HU: lung composition below, bone from HU_BONE_FROM
+HU_BONE_FROM = 250.0
+
+
+def hu_to_phantom(hu: np.ndarray, voxel_cm: float) -> Phantom:
+    """Density by the calibration curve, material by HU thresholds: lung (water
+    composition; air is lung at 0.0012 g/cm^3) below -400 HU, bone from 250 HU,
+    soft tissue (MATERIALS_PAPER) between."""
+    xs = np.array([p[0] for p in HU_CALIBRATION])
+    ys = np.array([p[1] for p in HU_CALIBRATION])
+    h = np.clip(hu.astype(np.float64), xs[0], xs[-1])
+    rho = np.interp(h, xs, ys).astype(np.float32)
+    mat = np.full(hu.shape, MAT_TISSUE, dtype=np.uint8)
+    mat[h < HU_LUNG_BELOW] = MAT_LUNG
+    mat[h >= HU_BONE_FROM] = MAT_BONE
+    nz, ny, nx = hu.shape
+    return Phantom((nx, ny, nz), (voxel_cm,) * 3, mat, rho)
+
+
+def synthetic_ct_hu(dims: Sequence[int], voxel_cm: float, seed: int) -> np.ndarray:
+    """A seeded thorax-like HU volume (z = beam depth, the body axis along y):
+    an elliptic soft-tissue body (40 HU) in air, two lungs (-750 HU), a spine
+    behind them and a sternum in front (1200 HU), with Gaussian noise of 20 HU
+    (CT-like) everywhere inside the body."""
+    nx, ny, nz = dims
+    rng = np.random.default_rng(seed)
+    z = (np.arange(nz) + 0.5) * voxel_cm
+    x = (np.arange(nx) + 0.5) * voxel_cm
+    Z, X = np.meshgrid(z, x, indexing="ij")  # (nz, nx): the transverse slice
+    cz, cx = nz * voxel_cm / 2, nx * voxel_cm / 2
+    az, ax = 0.42 * nz * voxel_cm, 0.46 * nx * voxel_cm
+    body = ((Z - cz) / az) ** 2 + ((X - cx) / ax) ** 2 <= 1.0
+    hu2 = np.where(body, 40.0, -1000.0)
+    for sx in (-1.0, 1.0):  # lungs
+        lung = ((Z - cz) / (0.55 * az)) ** 2 + ((X - cx - sx * 0.45 * ax) / (0.36 * ax)) ** 2 <= 1.0
+        hu2 = np.where(lung & body, -750.0, hu2)
+    spine = ((Z - (cz + 0.72 * az)) / (0.14 * az)) ** 2 + ((X - cx) / (0.12 * ax)) ** 2 <= 1.0
+    sternum = (np.abs(Z - (cz - 0.86 * az)) <= 0.05 * az) & (np.abs(X - cx) <= 0.12 * ax)
+    hu2 = np.where((spine | sternum) & body, 1200.0, hu2)
+    hu = np.repeat(hu2[:, None, :], ny, axis=1)
+    noise = rng.normal(0.0, 20.0, size=hu.shape)
+    return np.where(hu > -1000.0, hu + noise, hu)
+
+
+def synthetic_ct(particle: int, n_histories: Optional[int] = None, dims: Sequence[int] = (128, 96, 128),
+                 voxel_cm: float = 0.25, seed: int = 6) -> Plan:
+    """A synthetic-CT plan: the seeded thorax HU volume through the calibration,
+    a 10x10 cm^2 field entering the front (z = 0) through the sternum side: the
+    6 MV-like spectrum for photons (4e6), 15 MeV for electrons (1e6)."""
+    ph = hu_to_phantom(synthetic_ct_hu(dims, voxel_cm, seed), voxel_cm)
+    X, Y, _ = ph.extent_cm
+    if particle == PHOTON:
+        edges, w = synthetic_6mv_spectrum(seed=3)
+        src = Source(PHOTON, BEAM_SQUARE, center_cm=(X / 2, Y / 2), field_cm=10.0,
+                     spectrum_edges=edges, spectrum_weights=w)
+    else:
+        src = square_field(ELECTRON, 15.0, ph, 10.0)
+    name = "synthetic_ct_thorax_" + ("photon_6MV" if particle == PHOTON else "electron_15MeV")
+    return Plan(name, ph, src, n_histories or (4_000_000 if particle == PHOTON else 1_000_000), seed)
+
+
 def config3(n_histories: int = 10_000_000, n: int = 256, voxel_cm: float = 0.2,
             seed: int = 3) -> Plan:
     """Water / bone / lung / water slabs of 3 / 2 / 6 / rest cm on 256^3 at 0.2 cm,
