@@ -48,6 +48,8 @@ def parse():
                          "paper's three geometries, each beam alone (Table resabsexec); ablation: "
                          "the lane refill policies on the second geometry (Table resdivred); "
                          "kerma: the photon-only mode against full transport on the c2 photon beam")
+    ap.add_argument("--small", action="store_true",
+                    help="ablation: 1/5 of the histories (a small case for ncu)")
     ap.add_argument("--graph", action="store_true",
                     help="launch each sequence's first launch from a captured CUDA graph")
     ap.add_argument("--requests", type=int, default=1000, help="served: number of requests")
@@ -540,6 +542,8 @@ def run_ablation(args):
     rows = []
     for particle in (W.ELECTRON, W.PHOTON):
         pl = W.geom2(particle)
+        if args.small:
+            pl.n_histories //= 5
         pid = ctx.create_phantom(pl.phantom)
         plan = ctx.plan_open(pid, pl.source, pl.seed, 32)
         d = torch.zeros(pl.phantom.nvox, dtype=torch.float64, device="cuda")
