@@ -257,34 +257,6 @@ def run_ours(args):
     total_ms = max_over_ranks(sum(ms), dist, dev)
     value = (N_E + N_G) * args.steps * world / (total_ms / 1e3)
 
-    # the same step as one batched launch of both plans (the batched form on
-    # this workload; each plan's tally is bit-identical to its plain run)
-    def step_one_launch(i):
-        se = rank_seed(rank, i)
-        ctx.plan_reset(plan_e, se, sh)
-        ctx.plan_reset(plan_g, se + 1, sh)
-        ctx.run([plan_e, plan_g], [N_E, N_G], sh)
-        st_e = ctx.plan_result(plan_e, 0.5, out["de"].data_ptr(), out["se"].data_ptr(), sh)
-        st_g = ctx.plan_result(plan_g, 0.5, out["dg"].data_ptr(), out["sg"].data_ptr(), sh)
-        return st_e, st_g
-
-    for i in range(args.warmup):
-        step_one_launch(-1 - i)
-    ev1 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    st1 = None
-    for i in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-            ev1[i][0].record(stream)
-            st1 = step_one_launch(i)
-            ev1[i][1].record(stream)
-    torch.cuda.synchronize()
-    ms1 = sum(a.elapsed_time(b) for a, b in ev1) / args.steps
-    one_launch = {"value": (N_E + N_G) * world / (ms1 / 1e3), "ms_per_step": ms1,
-                  "over_plain": (total_ms / args.steps) / ms1, "transport_ms": st1[0]["transport_ms"]}
-
     # end to end through the C ABI with host buffers: each step uploads the
     # phantom from pinned host memory, runs both beams through gpumcd_simulate
     # and reads dose and sigma back into pinned host memory
@@ -342,8 +314,7 @@ def run_ours(args):
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "host_memory": "pinned"},
             "gpu_launches": launches,
-            "clocks": clocks,
-            "batched_one_launch": one_launch}
+            "clocks": clocks}
     if cpu:
         line["cpu_baseline"] = {"value": cpu[0], "unit": UNIT, "cores": cpu[1], "kind": "oracle",
                                 "sample": cpu[2]}
@@ -403,7 +374,10 @@ def run_batched(args):
         st = [ctx.plan_result(p, 0.5) for p in plans]
         ev[1].record()
         torch.cuda.synchronize()
-        return ev[0].elapsed_time(ev[1]), st[0]["transport_ms"], st
+        # a set of both particle types runs as one sequence per type: its
+        # transport time is the sum of the two sequences'
+        per_type = {sp.particle: x["transport_ms"] for sp, x in zip(specs, st)}
+        return ev[0].elapsed_time(ev[1]), sum(per_type.values()), st
 
     def plain():
         tot = tr = 0.0

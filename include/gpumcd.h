@@ -223,7 +223,11 @@ gpumcd_status gpumcd_plan_reset(gpumcd_ctx *ctx, int32_t plan_id, uint64_t seed,
 /* One batched persistent launch (sequence): plan plan_ids[i] simulates its next
  * n_histories[i] histories, for n_plans <= GPUMCD_MAX_PLANS_PER_RUN distinct
  * plans (host arrays).  Enqueued on `stream`; returns once the launch sequence
- * has finished. */
+ * has finished.  A set holding both electron and photon plans runs as two
+ * sequences, the electron plans' then the photon plans' (one launch drawing
+ * both kinds of primaries is slower); each plan's transport_ms is then its own
+ * sequence's, and gpumcd_debug_counters reports the second.  The whole set is
+ * validated before anything runs. */
 gpumcd_status gpumcd_run(gpumcd_ctx *ctx, int32_t n_plans, const int32_t *plan_ids,
                          const uint64_t *n_histories, void *stream);
 

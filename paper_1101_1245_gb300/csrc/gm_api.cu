@@ -914,6 +914,36 @@ gpumcd_status gpumcd_run(gpumcd_ctx *c, int32_t n_plans, const int32_t *ids, con
     if (!c) return GPUMCD_ERR_INVALID_ARG;
     Slot &sl = c->slot[0];
     if (sl.busy) return GPUMCD_ERR_STATE;
+    // A set holding both electron and photon plans runs as one sequence per
+    // particle type, electrons first.  In one launch the warps would draw both
+    // kinds of primaries at once and switch type far more often; on the C4
+    // set that cost as much as batching saves (388 vs 375 ms).  The tallies do
+    // not depend on the split.  The whole set is validated before anything
+    // runs, so a rejected set runs nothing.
+    if (n_plans > 1 && n_plans <= GPUMCD_MAX_PLANS_PER_RUN && ids && n_hist) {
+        std::vector<int32_t> id_t[2];
+        std::vector<uint64_t> n_t[2];
+        bool ok = true;
+        for (int i = 0; i < n_plans && ok; ++i) {
+            auto it = c->plans.find(ids[i]);
+            if (it == c->plans.end() || it->second.failed || it->second.hist_sub + n_hist[i] > (1ull << 32)) {
+                ok = false;
+                break;
+            }
+            for (int j = 0; j < i; ++j)
+                if (ids[j] == ids[i]) ok = false;
+            const int t = it->second.particle == GPUMCD_ELECTRON ? 0 : 1;
+            id_t[t].push_back(ids[i]);
+            n_t[t].push_back(n_hist[i]);
+        }
+        if (ok && !id_t[0].empty() && !id_t[1].empty()) {
+            for (int t = 0; t < 2; ++t) {
+                ST(seq_start(c, sl, (int32_t)id_t[t].size(), id_t[t].data(), n_t[t].data(), pick(c, stream)));
+                ST(seq_finish(c, sl));
+            }
+            return GPUMCD_OK;
+        }
+    }
     ST(seq_start(c, sl, n_plans, ids, n_hist, pick(c, stream)));
     return seq_finish(c, sl);
 }

@@ -117,6 +117,7 @@ class Server:
         self.results: List[DoseResult] = []
         self.total_histories = 0
         self.rounds = 0
+        self._turn = 0
         self.max_active = 0
         self.max_used = 0
         self.folds = 0
@@ -174,12 +175,25 @@ class Server:
         return [a for a in self.active.values()
                 if a.submitted < max(a.next_check, 1) and a.submitted < a.req.max_histories]
 
+    @staticmethod
+    def _kind(a: "_Active") -> int:
+        return int(getattr(a.req.source, "particle", 0))
+
     def _submit_rounds(self) -> None:
-        """Fill the free launch slots with rounds over the plans that have work."""
+        """Fill the free launch slots with rounds over the plans that have work.
+        A round carries one particle type, the types taking turns: a launch that
+        draws electron and photon primaries at once is slower (its warps switch
+        type far more often), and with two rounds in flight both types still run
+        together, each in its own launch."""
         while len(self.inflight) < self.depth:
             plans = self._runnable()
             if not plans:
                 return
+            kinds = sorted({self._kind(a) for a in plans})
+            if len(kinds) > 1:
+                k = kinds[self._turn % len(kinds)]
+                self._turn += 1
+                plans = [a for a in plans if self._kind(a) == k]
             share = max(self.round_histories // len(plans), self._quantum())
             chunks = [self._chunk(a, share) for a in plans]
             ticket = self.ctx.submit([a.plan for a in plans], chunks)

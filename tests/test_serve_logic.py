@@ -133,3 +133,34 @@ def test_alone_follows_the_same_schedule():
     r = run_alone(ctx, DoseRequest(0, 0, 1000, None, 7), target=0.01, first_chunk=10_000)
     assert r.s_thr <= 0.01 and r.histories >= (2.5 / 0.01) ** 2
     assert all(n % 16 == 0 for n in ctx.chunks)
+
+
+def test_rounds_carry_one_particle_type_in_turn():
+    """A round holds plans of one particle type, the types taking turns, and
+    every request of either type still reaches the target."""
+    import types
+    ctx = FakeCtx({k: 2.0 for k in range(5)})
+    rounds = []
+    submit = ctx.submit
+
+    def spy(plans, ns):
+        rounds.append(list(plans))
+        return submit(plans, ns)
+
+    ctx.submit = spy
+    srv = Server(ctx, hbm_budget=1 << 40, target=0.02, round_histories=100_000, first_chunk=5_000,
+                 clock=Clock())
+    kind = {}
+    for i in range(10):
+        src = types.SimpleNamespace(particle=i % 2)
+        r = DoseRequest(i, i % 5, 1000, src, 100 + i)
+        srv.submit(r)
+        kind[i] = i % 2
+    res = srv.run(real_time=False)
+    assert sorted(r.rid for r in res) == list(range(10))
+    # plans open in admission order, which is request order here (the budget admits all)
+    opened = sorted({p for rnd in rounds for p in rnd})
+    plan_kind = {p: kind[rid] for rid, p in enumerate(opened)}
+    mixed = [rnd for rnd in rounds if len({plan_kind[p] for p in rnd}) > 1]
+    assert not mixed
+    assert {plan_kind[rounds[0][0]], plan_kind[rounds[1][0]]} == {0, 1}  # the types alternate
