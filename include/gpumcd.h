@@ -54,6 +54,7 @@ typedef int32_t gpumcd_status;
 #define GPUMCD_ELECTRON 1
 #define GPUMCD_BEAM_PENCIL 0
 #define GPUMCD_BEAM_SQUARE 1
+#define GPUMCD_BEAM_PHASE_SPACE 2 /* primaries listed by the caller, history h taking record h mod n */
 
 /* Energy unit of the ledgers and of the dose tally: 2^-26 MeV. */
 #define GPUMCD_ENERGY_QUANTUM_MEV (1.0 / 67108864.0)
@@ -92,6 +93,16 @@ typedef struct {
     const double *spectrum_weights;
     double center_cm[2];
     double field_cm;
+    /* GPUMCD_BEAM_PHASE_SPACE (the paper's outlook, §V): n_phase_space records
+     * of 7 doubles, x, y, z (cm), ux, uy, uz (normalised on upload), E (MeV,
+     * in (0, e_max]), all of `particle`; history h starts as record h mod n.
+     * Host array, copied at gpumcd_plan_open; energy and spectrum are ignored.
+     * A launch holding such a plan runs a separately compiled kernel
+     * (blocks_per_sm <= 2, none of the GPUMCD_LAUNCH_PROFILE,
+     * GPUMCD_LAUNCH_WARP_AGGREGATE, GPUMCD_LAUNCH_KERMA flags nor a
+     * refill_period other than 1: else GPUMCD_ERR_INVALID_ARG at run time). */
+    int32_t n_phase_space;
+    const double *phase_space;
 } gpumcd_source;
 
 /* Launch tuning; 0 in a field keeps the current value.  See gpumcd_set_launch. */

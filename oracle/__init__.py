@@ -68,7 +68,7 @@ class SourceC(C.Structure):
     _fields_ = [("particle", C.c_int32), ("beam", C.c_int32), ("energy", C.c_double),
                 ("n_spec", C.c_int32), ("spec_edges", C.POINTER(C.c_double)),
                 ("spec_weights", C.POINTER(C.c_double)), ("cx", C.c_double), ("cy", C.c_double),
-                ("field", C.c_double)]
+                ("field", C.c_double), ("n_phsp", C.c_int32), ("phsp", C.POINTER(C.c_double))]
 
 
 class Stats(C.Structure):
@@ -199,6 +199,14 @@ def source(src, keep: _Keep) -> SourceC:
         s.spec_weights = w.ctypes.data_as(_DP)
     else:
         s.n_spec = 0
+    ps = getattr(src, "phase_space", None)
+    if ps is not None:
+        a = np.ascontiguousarray(ps, dtype=np.float64).reshape(-1, 7)
+        keep.refs.append(a)
+        s.n_phsp = len(a)
+        s.phsp = a.ctypes.data_as(_DP)
+    else:
+        s.n_phsp = 0
     return s
 
 

@@ -60,12 +60,14 @@ typedef struct {
 
 typedef struct {
     int32_t particle; /* 0 photon, 1 electron */
-    int32_t beam;     /* 0 pencil, 1 square field */
+    int32_t beam;     /* 0 pencil, 1 square field, 2 phase space */
     double energy;    /* MeV (mono) */
     int32_t n_spec;   /* >0: histogram spectrum with n_spec bins */
     const double *spec_edges;
     const double *spec_weights;
     double cx, cy, field;
+    int32_t n_phsp;      /* beam 2: records */
+    const double *phsp;  /* beam 2: [n_phsp][7] x, y, z (cm), ux, uy, uz, E (MeV) */
 } om_source;
 
 typedef struct {

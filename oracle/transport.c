@@ -616,6 +616,17 @@ static int validate(const om_material *mats, int32_t n_mat, const om_physics *ph
                     const om_phantom *ph, const om_source *src) {
     if (!mats || n_mat < 1 || n_mat > OM_MAX_MATERIALS || !phys || !ph || !src) return -1;
     if (ph->nx < 1 || ph->ny < 1 || ph->nz < 1 || !(ph->dx > 0 && ph->dy > 0 && ph->dz > 0)) return -1;
+    if (src->beam == 2) {
+        if (src->n_phsp < 1 || !src->phsp) return -1;
+        for (int32_t i = 0; i < src->n_phsp; ++i) {
+            const double *r = src->phsp + 7 * (size_t)i;
+            for (int a = 0; a < 7; ++a)
+                if (!isfinite(r[a])) return -1;
+            if (!(r[6] > 0.0 && r[6] <= phys->e_max)) return -1;
+            if (!(r[3] * r[3] + r[4] * r[4] + r[5] * r[5] > 0.0)) return -1;
+        }
+        return 0;
+    }
     if (src->n_spec < 0) return -1;
     if (src->n_spec == 0 && !(src->energy > 0.0 && src->energy <= phys->e_max)) return -1;
     if (src->n_spec > 0 && !(src->spec_edges[src->n_spec] <= phys->e_max)) return -1;
@@ -653,10 +664,25 @@ static void ctx_free(ctx_t *c) {
 }
 
 /* Primary particle of history h (§II.C.2, initParticle): a pencil or square
- * parallel beam entering through z = 0 along +z; mono energy or a spectrum. */
+ * parallel beam entering through z = 0 along +z, mono energy or a spectrum;
+ * or, for a phase-space source, record h mod n as given (direction
+ * normalised). */
 static void make_primary(ctx_t *c, const om_source *src, const double *cdf, uint64_t h,
                          part_t *p, stream_t *s) {
     stream_init(s, c->seed, h, 1ull, 0);
+    if (src->beam == 2) {
+        const double *r = src->phsp + 7 * (h % (uint64_t)src->n_phsp);
+        const double nu = sqrt(r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
+        for (int a = 0; a < 3; ++a) {
+            p->x[a] = r[a];
+            p->u[a] = r[3 + a] / nu;
+        }
+        p->E = r[6];
+        p->type = src->particle;
+        p->lin = 1ull;
+        p->draw = s->draw;
+        return;
+    }
     p->x[0] = src->cx;
     p->x[1] = src->cy;
     p->x[2] = 0.0;

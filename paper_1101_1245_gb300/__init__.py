@@ -25,7 +25,7 @@ MAX_PLANS_PER_RUN = 64
 MAX_INFLIGHT = 2
 ENERGY_QUANTUM_MEV = 1.0 / 67108864.0
 PHOTON, ELECTRON = 0, 1
-BEAM_PENCIL, BEAM_SQUARE = 0, 1
+BEAM_PENCIL, BEAM_SQUARE, BEAM_PHASE_SPACE = 0, 1, 2
 LAUNCH_WARP_AGGREGATE = 1
 LAUNCH_PROFILE = 2
 LAUNCH_GRAPH = 4
@@ -65,7 +65,8 @@ class Source(C.Structure):
     _fields_ = [("particle", C.c_int32), ("beam", C.c_int32), ("energy_mev", C.c_double),
                 ("n_spectrum", C.c_int32), ("spectrum_edges", C.POINTER(C.c_double)),
                 ("spectrum_weights", C.POINTER(C.c_double)), ("center_cm", C.c_double * 2),
-                ("field_cm", C.c_double)]
+                ("field_cm", C.c_double), ("n_phase_space", C.c_int32),
+                ("phase_space", C.POINTER(C.c_double))]
 
 
 class Launch(C.Structure):
@@ -200,6 +201,12 @@ class _SourceBox:
             self.s.n_spectrum = len(w)
             self.s.spectrum_edges = e.ctypes.data_as(C.POINTER(C.c_double))
             self.s.spectrum_weights = w.ctypes.data_as(C.POINTER(C.c_double))
+        ps = getattr(src, "phase_space", None)
+        if ps is not None:
+            a = np.ascontiguousarray(ps, dtype=np.float64).reshape(-1, 7)
+            self.keep.append(a)
+            self.s.n_phase_space = len(a)
+            self.s.phase_space = a.ctypes.data_as(C.POINTER(C.c_double))
 
 
 @dataclasses.dataclass

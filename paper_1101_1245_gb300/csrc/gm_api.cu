@@ -33,6 +33,7 @@ struct Plan {
     int32_t particle, beam;
     double energy, cx, cy, field;
     int32_t n_spec;
+    uint32_t n_phsp = 0;     // phase-space records (held in `spec`)
     uint64_t seed;
     uint32_t W;
     uint64_t hist_sub = 0;   // histories handed to launch sequences (numbering of the next run)
@@ -204,6 +205,8 @@ gpumcd_status set_device(gpumcd_ctx *c) {
 bool valid_source(const gpumcd_ctx *c, const gpumcd_source *s) {
     if (!s) return false;
     if (s->particle != GPUMCD_PHOTON && s->particle != GPUMCD_ELECTRON) return false;
+    if (s->beam == GPUMCD_BEAM_PHASE_SPACE)  // records are checked when copied
+        return s->n_phase_space >= 1 && s->n_phase_space <= (1 << 24) && s->phase_space;
     if (s->beam != GPUMCD_BEAM_PENCIL && s->beam != GPUMCD_BEAM_SQUARE) return false;
     if (!std::isfinite(s->center_cm[0]) || !std::isfinite(s->center_cm[1])) return false;
     if (s->beam == GPUMCD_BEAM_SQUARE && !(s->field_cm >= 0.0 && std::isfinite(s->field_cm))) return false;
@@ -539,6 +542,33 @@ gpumcd_status gpumcd_plan_open(gpumcd_ctx *c, int32_t phantom_id, const gpumcd_s
         }
     }
     dev_free(c, tmp);
+    if (st == GPUMCD_OK && p.beam == GPUMCD_BEAM_PHASE_SPACE) {
+        // records as float4 pairs (x, y, z, E) (ux, uy, uz, 0), direction normalised
+        const int32_t n = src->n_phase_space;
+        std::vector<float> h((size_t)n * 8);
+        for (int32_t i = 0; i < n && st == GPUMCD_OK; ++i) {
+            const double *r = src->phase_space + 7 * (size_t)i;
+            bool ok = true;
+            for (int a = 0; a < 7; ++a) ok = ok && std::isfinite(r[a]);
+            const double nu = std::sqrt(r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
+            if (!ok || !(nu > 0.0) || !(r[6] > 0.0 && r[6] <= c->phys.e_max)) {
+                st = GPUMCD_ERR_INVALID_ARG;
+                break;
+            }
+            float *o = h.data() + 8 * (size_t)i;
+            o[0] = (float)r[0], o[1] = (float)r[1], o[2] = (float)r[2], o[3] = (float)r[6];
+            o[4] = (float)(r[3] / nu), o[5] = (float)(r[4] / nu), o[6] = (float)(r[5] / nu), o[7] = 0.f;
+        }
+        if (st == GPUMCD_OK) st = dev_alloc(c, p.spec, h.size() * sizeof(float));
+        if (st == GPUMCD_OK) {
+            cudaError_t e = cudaMemcpyAsync(p.spec.p, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice,
+                                            c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) st = cuda_status(e);
+        }
+        p.n_phsp = (uint32_t)n;
+        p.n_spec = 0;
+    }
     if (st == GPUMCD_OK) {
         cudaError_t e = cudaMemsetAsync(p.tally.p, 0, (size_t)n_batches * nvox * 8, c->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(p.ledger.p, 0, 4 * 8, c->stream);
@@ -809,6 +839,8 @@ gpumcd_status seq_start(gpumcd_ctx *c, Slot &sl, int32_t n_plans, const int32_t 
         d.src_type = p.particle;
         d.beam = p.beam;
         d.e_src_q = (uint32_t)std::llround(p.energy / kQ);
+        d.n_phsp = p.n_phsp;
+        if (p.n_phsp) A.phsp = 1;
         d.hist_base = p.hist_sub;
         d.n_hist = n_hist[i];
         const int t = p.particle;
@@ -828,6 +860,10 @@ gpumcd_status seq_start(gpumcd_ctx *c, Slot &sl, int32_t n_plans, const int32_t 
     A.switch_high = c->launch.switch_high;
     A.refill_low = c->launch.refill_low;
     A.refill_period = c->launch.refill_period;
+    // the phase-space kernel is compiled for up to 512 threads x 2 CTAs per SM, alone
+    if (A.phsp && (c->launch.blocks_per_sm > 2 || c->launch.refill_period != 1u ||
+                   (c->launch.flags & (GPUMCD_LAUNCH_PROFILE | GPUMCD_LAUNCH_WARP_AGGREGATE | GPUMCD_LAUNCH_KERMA))))
+        return GPUMCD_ERR_INVALID_ARG;
     A.chunk = c->launch.chunk;
     A.flags = c->launch.flags;
     A.counters = dc->counters;

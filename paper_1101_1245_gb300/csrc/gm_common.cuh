@@ -97,7 +97,7 @@ struct __align__(16) PlanDev {
     float Z, cx, cy, field;
     uint32_t nvox, bmask, key_lo, key_hi;
     int32_t src_type, beam;
-    uint32_t e_src_q, pad0;
+    uint32_t e_src_q, n_phsp;     // n_phsp: phase-space records (spec holds them)
     unsigned long long hist_base;  // first history of this launch
     unsigned long long n_hist;     // histories in this launch
 };
@@ -127,6 +127,7 @@ struct TransportArgs {
     uint32_t stack_cap, switch_high, refill_low, chunk;
     uint32_t flags;
     uint32_t refill_period;            // 1: refill every pass; N: every N-th pass or when empty
+    uint32_t phsp, pad_phsp;           // a plan of the launch has a phase-space source
     unsigned long long *counters;      // run counters (see CNT_*)
     int32_t *error;                    // device status word
 };

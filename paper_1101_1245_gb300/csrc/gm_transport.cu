@@ -355,7 +355,10 @@ __device__ __forceinline__ float sample_spectrum(const PlanDev &P, float z) {
 }
 
 // Primary of history h of plan P (§II.C.2 initParticle): pencil or square
-// parallel beam entering through z = 0 along +z.
+// parallel beam entering through z = 0 along +z; with PHSP, a phase-space
+// plan's primary is record h mod n as listed (the first draw is still taken,
+// so the draw counter starts where the beams' does).
+template <bool PHSP>
 __device__ __forceinline__ uint32_t make_primary(Lane &p, const PlanDev &P, uint32_t plan, uint64_t h) {
     p.hist = (uint32_t)h;
     p.lin_lo = 1u;
@@ -363,6 +366,20 @@ __device__ __forceinline__ uint32_t make_primary(Lane &p, const PlanDev &P, uint
     p.draw = 0u;
     p.plan = plan;
     const uint4 r = draw4(p, P);
+    if (PHSP && P.beam == GPUMCD_BEAM_PHASE_SPACE) {
+        const float4 *ps = reinterpret_cast<const float4 *>(P.spec);
+        const uint32_t k = (uint32_t)(h % (unsigned long long)P.n_phsp);
+        const float4 a = __ldg(ps + 2 * (size_t)k), b = __ldg(ps + 2 * (size_t)k + 1);
+        p.x = a.x;
+        p.y = a.y;
+        p.z = a.z;
+        p.ux = b.x;
+        p.uy = b.y;
+        p.uz = b.z;
+        p.E = __float2uint_rn(a.w * kInvQf);
+        p.act = true;
+        return p.E;
+    }
     p.x = P.cx;
     p.y = P.cy;
     if (P.beam == GPUMCD_BEAM_SQUARE) {
@@ -760,7 +777,7 @@ __device__ void spill_to_queue(const TransportArgs &A, const Smem &S, int gw, in
 
 // Fill empty lanes with particles of type t.  Returns the number of lanes
 // that hold a particle afterwards.
-template <bool KERMA>
+template <bool KERMA, bool PHSP>
 __device__ int refill(const TransportArgs &A, const Smem &S, CtaFlags &F, Lane &p, int gw, int w, int t) {
     const int lane = threadIdx.x & 31;
     WarpState &ws = S.ws[w];
@@ -831,7 +848,7 @@ __device__ int refill(const TransportArgs &A, const Smem &S, CtaFlags &F, Lane &
             }
             const uint32_t plan = A.prim_plan[t][a];
             const PlanDev &P = S.plans[plan];
-            ledger_add(S, plan, 0, make_primary(p, P, plan, P.hist_base + (g - A.prim_off[t][a])));
+            ledger_add(S, plan, 0, make_primary<PHSP>(p, P, plan, P.hist_base + (g - A.prim_off[t][a])));
             if (KERMA && t == 1) {
                 // photon-only mode: a primary electron deposits where it enters
                 if (inside(P, p.x, p.y, p.z)) {
@@ -929,10 +946,10 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
 
 // PROF compiles in the per-type cycle profile (GPUMCD_LAUNCH_PROFILE), AGG
 // the warp-aggregated deposit (GPUMCD_LAUNCH_WARP_AGGREGATE), SCHED the
-// refill policies of the divergence-reduction ablation (refill_period != 1)
-// and KERMA the photon-only mode (GPUMCD_LAUNCH_KERMA); the production
-// instantiations carry none of them.
-template <int MAXT, int MINB, bool PROF, bool AGG, bool SCHED, bool KERMA>
+// refill policies of the divergence-reduction ablation (refill_period != 1),
+// KERMA the photon-only mode (GPUMCD_LAUNCH_KERMA) and PHSP phase-space
+// sources; the production instantiations carry none of them.
+template <int MAXT, int MINB, bool PROF, bool AGG, bool SCHED, bool KERMA, bool PHSP>
 __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant__ TransportArgs A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *tab = (float *)smem_raw;
@@ -1023,10 +1040,10 @@ __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant_
                 n_act = __popc(actm);
                 fresh = false;
             } else {
-                n_act = refill<KERMA>(A, S, F, p, gw, w, t);
+                n_act = refill<KERMA, PHSP>(A, S, F, p, gw, w, t);
             }
         } else {
-            n_act = refill<KERMA>(A, S, F, p, gw, w, t);
+            n_act = refill<KERMA, PHSP>(A, S, F, p, gw, w, t);
         }
         if (prof && lane == 0) atomicAdd(&S.cnt[CNT_PROF_REFILL_CYC], (unsigned long long)(clock64() - c0));
         const int o = 1 - t;
@@ -1128,25 +1145,27 @@ size_t transport_smem_bytes(int /*block_threads*/) {
 typedef void (*TransportKernel)(const TransportArgs);
 struct Variant {
     int max_threads, min_blocks;
-    bool prof, agg, sched, kerma;
+    bool prof, agg, sched, kerma, phsp;
     TransportKernel fn;
 };
 static const Variant kVariants[] = {
-    {512, 1, false, false, false, false, k_transport<512, 1, false, false, false, false>},
-    {384, 2, false, false, false, false, k_transport<384, 2, false, false, false, false>},
-    {512, 2, false, false, false, false, k_transport<512, 2, false, false, false, false>},
-    {256, 3, false, false, false, false, k_transport<256, 3, false, false, false, false>},
-    {256, 4, false, false, false, false, k_transport<256, 4, false, false, false, false>},
-    {512, 2, true, false, false, false, k_transport<512, 2, true, false, false, false>},
-    {512, 2, false, true, false, false, k_transport<512, 2, false, true, false, false>},
-    {512, 2, false, false, true, false, k_transport<512, 2, false, false, true, false>},
-    {512, 2, false, false, false, true, k_transport<512, 2, false, false, false, true>},
+    {512, 1, false, false, false, false, false, k_transport<512, 1, false, false, false, false, false>},
+    {384, 2, false, false, false, false, false, k_transport<384, 2, false, false, false, false, false>},
+    {512, 2, false, false, false, false, false, k_transport<512, 2, false, false, false, false, false>},
+    {256, 3, false, false, false, false, false, k_transport<256, 3, false, false, false, false, false>},
+    {256, 4, false, false, false, false, false, k_transport<256, 4, false, false, false, false, false>},
+    {512, 2, true, false, false, false, false, k_transport<512, 2, true, false, false, false, false>},
+    {512, 2, false, true, false, false, false, k_transport<512, 2, false, true, false, false, false>},
+    {512, 2, false, false, true, false, false, k_transport<512, 2, false, false, true, false, false>},
+    {512, 2, false, false, false, true, false, k_transport<512, 2, false, false, false, true, false>},
+    {512, 2, false, false, false, false, true, k_transport<512, 2, false, false, false, false, true>},
 };
 
-static TransportKernel pick_variant(int block, int blocks_per_sm, bool prof, bool agg, bool sched, bool kerma) {
+static TransportKernel pick_variant(int block, int blocks_per_sm, bool prof, bool agg, bool sched, bool kerma,
+                                    bool phsp) {
     for (const Variant &v : kVariants)
-        if (v.prof == prof && v.agg == agg && v.sched == sched && v.kerma == kerma && block <= v.max_threads &&
-            blocks_per_sm <= v.min_blocks)
+        if (v.prof == prof && v.agg == agg && v.sched == sched && v.kerma == kerma && v.phsp == phsp &&
+            block <= v.max_threads && blocks_per_sm <= v.min_blocks)
             return v.fn;
     return nullptr;
 }
@@ -1163,7 +1182,7 @@ cudaError_t transport_configure(int block_threads) {
 cudaError_t launch_transport(const TransportArgs &a, int grid, int block, int blocks_per_sm, cudaStream_t s) {
     TransportKernel fn = pick_variant(block, blocks_per_sm, (a.flags & GPUMCD_LAUNCH_PROFILE) != 0u,
                                       (a.flags & GPUMCD_LAUNCH_WARP_AGGREGATE) != 0u, a.refill_period != 1u,
-                                      (a.flags & GPUMCD_LAUNCH_KERMA) != 0u);
+                                      (a.flags & GPUMCD_LAUNCH_KERMA) != 0u, a.phsp != 0u);
     if (!fn) return cudaErrorInvalidConfiguration;
     fn<<<grid, block, transport_smem_bytes(block), s>>>(a);
     return cudaGetLastError();

@@ -77,7 +77,7 @@ def test_refill_when_empty_matches_the_header():
 def test_struct_layouts_match_the_binding(tmp_path):
     """sizeof and field offsets of the ABI structs, from a C compiler reading
     the header, equal those of the binding's ctypes structures."""
-    structs = {"gpumcd_launch": g.Launch, "gpumcd_run_stats": g.RunStats}
+    structs = {"gpumcd_launch": g.Launch, "gpumcd_run_stats": g.RunStats, "gpumcd_source": g.Source}
     lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "gpumcd.h"', "int main(void) {"]
     for cname, cls in structs.items():
         lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')

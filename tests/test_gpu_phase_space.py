@@ -1,0 +1,99 @@
+"""Phase-space sources (GPUMCD_BEAM_PHASE_SPACE, the phase-space sources of the
+paper's outlook, §V): history h starts as record h mod n of a caller-supplied
+list.  Parity is against the oracle's own phase-space source on the same
+seeded records, with the bar of the other parity tests:
+- >= 99% of voxels above 10% of D_max within 3 combined sigma;
+- an exact integer ledger;
+- an incident energy equal to the records' energies taken in turn, in quanta."""
+import numpy as np
+import pytest
+
+import paper_1101_1245_gb300 as g
+import workloads as W
+from tests._stats import three_sigma_pass_rate
+from tests.gpu_common import ledger_exact, make_ctx, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+Q = 2.0 ** -26
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = make_ctx()
+    yield c
+    c.close()
+
+
+def _incident_quanta(src, n):
+    e = src.phase_space[:, 6].astype(np.float32)
+    q = np.rint(e.astype(np.float32) * np.float32(2 ** 26)).astype(np.uint64)
+    k = len(e)
+    return int(q.sum()) * (n // k) + int(q[: n % k].sum())
+
+
+CASES = [
+    ("electron_water", W.ELECTRON, lambda: W.homogeneous((32, 32, 40), 0.5, W.MAT_WATER, 1.0), 20_000),
+    ("photon_slabs", W.PHOTON, lambda: W.z_slabs((32, 32, 48), 0.5, [(3.0, W.MAT_WATER, 1.0),
+                                                                       (2.0, W.MAT_BONE, 1.85),
+                                                                       (6.0, W.MAT_LUNG, 0.26),
+                                                                       (1e9, W.MAT_WATER, 1.0)]), 100_000),
+]
+
+
+@pytest.mark.parametrize("name,particle,make_ph,n", CASES, ids=[c[0] for c in CASES])
+def test_phase_space_parity(ctx, name, particle, make_ph, n):
+    ph = make_ph()
+    src = W.point_source_phase_space(particle, ph, 997, seed=21, field_cm=8.0)
+    plan = W.Plan(name, ph, src, n, 31)
+    gpu = run_gpu(ctx, plan)
+    ora = run_oracle(plan)
+    assert ledger_exact(gpu.stats)
+    assert gpu.stats["e_incident"] == _incident_quanta(src, n)
+    do, so = ora.dose_gy(ph), ora.sigma_gy(ph)
+    mask = do > 0.1 * do.max()
+    assert mask.sum() > 100
+    rate = three_sigma_pass_rate(gpu.dose, gpu.sigma, do, so, mask)
+    assert rate >= 0.99, rate
+    key = "n_electron_steps" if particle == W.ELECTRON else "n_photon_real"
+    okey = "n_e_steps" if particle == W.ELECTRON else "n_photon_real"
+    assert gpu.stats[key] / n == pytest.approx(ora.stats[okey] / n, rel=0.03)
+
+
+def test_phase_space_of_the_pencil_matches_the_pencil(ctx):
+    """Records that all list the pencil beam's primary give the pencil run's
+    dose within statistics (a separately compiled kernel, the same physics)."""
+    ph = W.homogeneous((24, 24, 30), 0.5, W.MAT_WATER, 1.0)
+    pen = W.pencil(W.PHOTON, 3.0, 6.0, 6.0)
+    rec = np.repeat(np.array([[6.0, 6.0, 0.0, 0.0, 0.0, 1.0, 3.0]]), 3, axis=0)
+    phs = W.Source(W.PHOTON, W.BEAM_PHASE_SPACE, phase_space=rec)
+    a = run_gpu(ctx, W.Plan("pencil", ph, pen, 100_000, 5))
+    b = run_gpu(ctx, W.Plan("phsp", ph, phs, 100_000, 5))
+    assert a.stats["e_incident"] == b.stats["e_incident"]
+    mask = a.dose > 0.1 * a.dose.max()
+    assert three_sigma_pass_rate(b.dose, b.sigma, a.dose, a.sigma, mask) >= 0.99
+
+
+def test_phase_space_validation(ctx):
+    ph = W.homogeneous((8, 8, 8), 0.5, W.MAT_WATER, 1.0)
+    pid = ctx.create_phantom(ph)
+    try:
+        bad = np.array([[1.0, 1.0, 0.0, 0.0, 0.0, 1.0, 25.0]])  # above e_max
+        with pytest.raises(g.GpumcdError) as e:
+            ctx.plan_open(pid, W.Source(W.PHOTON, W.BEAM_PHASE_SPACE, phase_space=bad), 1, 16)
+        assert e.value.status == g.ERR_INVALID_ARG
+        zero = np.array([[1.0, 1.0, 0.0, 0.0, 0.0, 0.0, 2.0]])  # no direction
+        with pytest.raises(g.GpumcdError) as e:
+            ctx.plan_open(pid, W.Source(W.PHOTON, W.BEAM_PHASE_SPACE, phase_space=zero), 1, 16)
+        assert e.value.status == g.ERR_INVALID_ARG
+        good = np.array([[1.0, 1.0, 0.0, 0.0, 0.0, 1.0, 2.0]])
+        plan = ctx.plan_open(pid, W.Source(W.PHOTON, W.BEAM_PHASE_SPACE, phase_space=good), 1, 16)
+        ctx.set_launch(flags=g.LAUNCH_KERMA)  # no phase-space variant of the photon-only kernel
+        with pytest.raises(g.GpumcdError) as e:
+            ctx.run([plan], [64])
+        assert e.value.status == g.ERR_INVALID_ARG
+        ctx.set_launch(flags=0)
+        ctx.run([plan], [64])
+        assert ctx.plan_result(plan, 0.5)["histories"] == 64
+        ctx.plan_close(plan)
+    finally:
+        ctx.destroy_phantom(pid)

@@ -210,3 +210,30 @@ def test_woodcock_invariance_far_dense_voxel():
     mask = da > 0.1 * da.max()
     mask[23 * 16 * 16] = False  # the dense voxel itself
     assert three_sigma_pass_rate(da, sa, db, sb, mask) >= 0.98
+
+
+def test_phase_space_source_equals_the_beam_it_lists():
+    """A phase-space source (the paper's outlook, §V) whose every record is the
+    pencil beam's primary - same point, +z, same energy - gives the pencil
+    run's tallies exactly: record h mod n starts history h, and neither form
+    draws a random number for the primary."""
+    ph = W.homogeneous((12, 12, 20), 0.5, W.MAT_WATER, 1.0)
+    pen = W.pencil(W.PHOTON, 3.0, 3.0, 3.0)
+    rec = np.array([[3.0, 3.0, 0.0, 0.0, 0.0, 2.0, 3.0]])  # direction need not be unit length
+    phs = W.Source(W.PHOTON, W.BEAM_PHASE_SPACE, phase_space=np.repeat(rec, 5, axis=0))
+    a = oracle.simulate(W.MATERIALS, P, ph, pen, 2000, 9)
+    b = oracle.simulate(W.MATERIALS, P, ph, phs, 2000, 9)
+    assert np.array_equal(a.sum_e, b.sum_e) and np.array_equal(a.sum_e2, b.sum_e2)
+
+
+def test_phase_space_records_cycle_and_conserve_energy():
+    """History h takes record h mod n: the incident energy of N histories is the
+    sum of the records' energies taken in turn, and the ledger closes."""
+    ph = W.homogeneous((16, 16, 16), 0.5, W.MAT_WATER, 1.0)
+    src = W.point_source_phase_space(W.ELECTRON, ph, 7, seed=3, field_cm=4.0)
+    n = 50
+    r = oracle.simulate(W.MATERIALS, P, ph, src, n, 4)
+    want = sum(src.phase_space[h % 7, 6] for h in range(n))
+    st = r.stats
+    assert st["e_incident"] == pytest.approx(want, rel=1e-12)
+    assert st["e_deposited"] + st["e_escaped"] + st["e_rest"] == pytest.approx(st["e_incident"], rel=1e-9)

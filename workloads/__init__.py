@@ -136,21 +136,26 @@ class Phantom:
 
 
 PHOTON, ELECTRON = 0, 1
-BEAM_PENCIL, BEAM_SQUARE = 0, 1
+BEAM_PENCIL, BEAM_SQUARE, BEAM_PHASE_SPACE = 0, 1, 2
 
 
 @dataclasses.dataclass
 class Source:
     particle: int  # PHOTON or ELECTRON
-    beam: int  # BEAM_PENCIL or BEAM_SQUARE
+    beam: int  # BEAM_PENCIL, BEAM_SQUARE or BEAM_PHASE_SPACE
     energy: float = 0.0  # MeV, used when spectrum is None
     center_cm: Tuple[float, float] = (0.0, 0.0)  # beam centre on the z = 0 face
     field_cm: float = 0.0  # side of the square field
     spectrum_edges: Optional[np.ndarray] = None  # float64, n+1 bin edges (MeV)
     spectrum_weights: Optional[np.ndarray] = None  # float64, n bin weights
+    # BEAM_PHASE_SPACE: records (n, 7) = x, y, z (cm), ux, uy, uz, E (MeV), all of
+    # `particle`; history h starts as record h mod n
+    phase_space: Optional[np.ndarray] = None
 
     @property
     def max_energy(self) -> float:
+        if self.phase_space is not None:
+            return float(np.max(self.phase_space[:, 6]))
         if self.spectrum_edges is not None:
             return float(self.spectrum_edges[-1])
         return self.energy
@@ -235,6 +240,24 @@ def square_field(particle: int, energy: float, phantom: Phantom, field_cm: float
     X, Y, _ = phantom.extent_cm
     return Source(particle, BEAM_SQUARE, energy=energy, center_cm=(X / 2, Y / 2),
                   field_cm=field_cm)
+
+
+def point_source_phase_space(particle: int, phantom: "Phantom", n: int, seed: int,
+                             source_distance_cm: float = 30.0, field_cm: float = 8.0,
+                             e_lo: float = 1.0, e_hi: float = 12.0) -> Source:
+    """A seeded phase space standing in for a scored one: particles on the
+    z = 0 face, uniform over a square field, each aimed away from a point
+    source `source_distance_cm` above the face (a diverging beam), energies
+    uniform on [e_lo, e_hi] MeV."""
+    rng = np.random.default_rng(seed)
+    X, Y, _ = phantom.extent_cm
+    x = X / 2 + (rng.random(n) - 0.5) * field_cm
+    y = Y / 2 + (rng.random(n) - 0.5) * field_cm
+    d = np.stack([x - X / 2, y - Y / 2, np.full(n, source_distance_cm)], axis=1)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    e = e_lo + (e_hi - e_lo) * rng.random(n)
+    ps = np.column_stack([x, y, np.zeros(n), d, e])
+    return Source(particle, BEAM_PHASE_SPACE, phase_space=ps)
 
 
 def synthetic_6mv_spectrum(seed: int = 3, n_bins: int = 256, e_lo: float = 0.1,
