@@ -6,7 +6,7 @@
  * and the CPU-baseline leg of bench.py may load it.  It shares no code,
  * header, table or constant with the CUDA library.
  *
- * Model (same on both sides, stated in full in DESIGN.md's "readings"):
+ * Model (the same on both sides):
  *  - photons: analogue transport with Woodcock tracking (GPUMCD §II.A);
  *    Compton (Klein-Nishina, free electron), K-shell photoelectric with a
  *    Sauter photo-electron, pair production with no positrons and a uniform
