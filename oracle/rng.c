@@ -3,7 +3,7 @@
  * (J. K. Salmon et al., "Parallel random numbers: as easy as 1, 2, 3", SC'11).
  * TEST INFRASTRUCTURE ONLY (see oracle.h).
  *
- * GPUMCD §II.C.1 uses a combined multiply-with-carry generator; this build
+ * GPUMCD §II.C.1 uses a combined multiply-with-carry generator; this code
  * replaces it on both sides by a counter-based generator so that a particle's
  * random numbers depend only on (seed, history, lineage, draw index).
  *
