@@ -108,3 +108,21 @@ def test_config5_arrivals():
     reqs = W.config5(count=50, rate_per_s=20.0)
     t = np.array([r.arrival_s for r in reqs])
     assert (np.diff(t) > 0).all()
+
+
+def test_point_source_phase_space_recipe():
+    """Seeded records on the entry face, inside the field, unit directions
+    pointing away from the source point, energies in range."""
+    ph = W.homogeneous((40, 40, 10), 0.5, W.MAT_WATER, 1.0)
+    a = W.point_source_phase_space(W.PHOTON, ph, 500, seed=3, field_cm=8.0, e_lo=1.0, e_hi=12.0)
+    b = W.point_source_phase_space(W.PHOTON, ph, 500, seed=3, field_cm=8.0, e_lo=1.0, e_hi=12.0)
+    ps = a.phase_space
+    assert a.beam == W.BEAM_PHASE_SPACE and ps.shape == (500, 7) and np.array_equal(ps, b.phase_space)
+    assert np.all(ps[:, 2] == 0.0)
+    assert np.all(np.abs(ps[:, 0] - 10.0) <= 4.0) and np.all(np.abs(ps[:, 1] - 10.0) <= 4.0)
+    assert np.allclose(np.linalg.norm(ps[:, 3:6], axis=1), 1.0)
+    # each direction lies on the ray from the source point 30 cm above the field centre
+    src = np.array([10.0, 10.0, -30.0])
+    d = ps[:, 0:3] - src
+    assert np.allclose(d / np.linalg.norm(d, axis=1, keepdims=True), ps[:, 3:6])
+    assert ps[:, 6].min() >= 1.0 and ps[:, 6].max() <= 12.0 and a.max_energy == ps[:, 6].max()
