@@ -105,21 +105,6 @@ __device__ __forceinline__ uint32_t voxel_index(const PlanDev &P, float x, float
     return (uint32_t)ix + (uint32_t)P.nx * ((uint32_t)iy + (uint32_t)P.ny * (uint32_t)iz);
 }
 
-// A particle left exactly on a voxel face it is moving out through (its
-// distance to the exit is 0) is moved to the voxel it enters: face_step gives
-// the index change along one axis, +-1 when the coordinate lies within 4 FP32
-// ulps (in voxel units) of the face ahead of it in the direction of motion.
-// In FP32 a step that ends a nudge beyond a face at a grazing angle can round
-// back onto the face; indexed by position alone the particle would then stay
-// in the voxel it is leaving and creep on in nudge-sized steps (seen in thin
-// air, where nothing deflects it).
-__device__ __forceinline__ int face_step(float x, float inv_d, float u, int i) {
-    const float f = x * inv_d;
-    const float fr = f - (float)i;
-    const float eps = fmaxf(f, 1.0f) * (1.0f / 2097152.0f);  // 2^-21: 4 ulps of f
-    return (u < 0.f && fr < eps) ? -1 : ((u > 0.f && fr > 1.0f - eps) ? 1 : 0);
-}
-
 // Distance along the direction to the exit face of voxel (ix, iy, iz).
 __device__ __forceinline__ float exit_distance(const PlanDev &P, const Lane &p, int ix, int iy, int iz) {
     float dv = 3.0e38f;
@@ -127,6 +112,18 @@ __device__ __forceinline__ float exit_distance(const PlanDev &P, const Lane &p, 
     if (p.uy != 0.f) dv = fminf(dv, ((p.uy > 0.f ? (float)(iy + 1) : (float)iy) - p.y * P.inv_dy) * P.dy / p.uy);
     if (p.uz != 0.f) dv = fminf(dv, ((p.uz > 0.f ? (float)(iz + 1) : (float)iz) - p.z * P.inv_dz) * P.dz / p.uz);
     return dv;
+}
+
+// One float further along a direction cosine.  An electron step ends a nudge
+// past the face it aims at, but at a grazing angle nudge x cosine can fall
+// below FP32 resolution and the end point rounds back onto the face; indexed
+// by position, a particle crossing in the negative direction would then stay
+// in the voxel it is leaving, with a zero distance to its exit, and creep on
+// in nudge-sized steps (seen in thin air, where nothing deflects it).  Moving
+// every end coordinate one float along its direction takes it off the face.
+__device__ __forceinline__ float float_along(float x, float u) {
+    const int b = __float_as_int(x);
+    return u > 0.f ? __int_as_float(b + 1) : (u < 0.f ? __int_as_float(b - 1) : x);
 }
 
 // Fire-and-forget 64-bit add into the tally (no value comes back).
@@ -556,33 +553,8 @@ __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, in
         return false;
     }
     int ix, iy, iz;
-    uint32_t idx0 = voxel_index(P, p.x, p.y, p.z, ix, iy, iz);
-    uint32_t vw = __ldg(P.vox + idx0);
-    // distance to the voxel faces along u
-    float dv = exit_distance(P, p, ix, iy, iz);
-    if (dv <= 0.0f && p.draw >= 2u) {
-        // on the face it is leaving: FP32 rounded the last step's end back onto
-        // the face it crossed, and the particle belongs to the voxel it enters.
-        // A particle's first steps (draw counter below 2) keep the voxel of its
-        // position, so one created exactly on a face takes a nudge-length step
-        // across it first, as in FP64.
-        const int sx = face_step(p.x, P.inv_dx, p.ux, ix), sy = face_step(p.y, P.inv_dy, p.uy, iy),
-                  sz = face_step(p.z, P.inv_dz, p.uz, iz);
-        if (sx | sy | sz) {
-            ix += sx;
-            iy += sy;
-            iz += sz;
-            if ((unsigned)ix >= (unsigned)P.nx || (unsigned)iy >= (unsigned)P.ny || (unsigned)iz >= (unsigned)P.nz) {
-                ledger_add(S, p.plan, 1, p.E);
-                p.act = false;
-                return false;
-            }
-            idx0 = (uint32_t)ix + (uint32_t)P.nx * ((uint32_t)iy + (uint32_t)P.ny * (uint32_t)iz);
-            vw = __ldg(P.vox + idx0);
-            dv = exit_distance(P, p, ix, iy, iz);
-        }
-    }
-    dv = fmaxf(dv, 0.0f) + ph.nudge;
+    const uint32_t idx0 = voxel_index(P, p.x, p.y, p.z, ix, iy, iz);
+    const uint32_t vw = __ldg(P.vox + idx0);
     const int m0 = vw & (NMAT - 1);
     const float rho0 = (float)(vw >> 4) * kRhoQ;
     if (p.E < ph.e_abs_q) {
@@ -595,6 +567,9 @@ __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, in
     const float xe = fmaf(__log2f((float)p.E), ph.grid.el_a, ph.grid.el_bq);
     const float L0 = rho0 * interp(te, xe);
     const float smax = ph.estepe * T / L0;
+    // distance to the voxel faces along u, plus the nudge
+    float dv = exit_distance(P, p, ix, iy, iz);
+    dv = fmaxf(dv, 0.0f) + ph.nudge;
     const float sig_hat = interp_ldg(P.maj + G, xe);
     const uint4 r = draw4(p, P);
     const float ehard = -__logf(u01(r.x)) / sig_hat;
@@ -622,9 +597,10 @@ __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, in
     dep_idx = idx0;  // the hinge lies in the step-start voxel
     dep_e = dq;
     const float l2 = es - l1;
-    p.x = fmaf(l2, p.ux, x);
-    p.y = fmaf(l2, p.uy, y);
-    p.z = fmaf(l2, p.uz, z);
+    // each coordinate one float further along the direction (float_along)
+    p.x = float_along(fmaf(l2, p.ux, x), p.ux);
+    p.y = float_along(fmaf(l2, p.uy, y), p.uy);
+    p.z = float_along(fmaf(l2, p.uz, z), p.uz);
     p.E = e1;
     if (!inside(P, p.x, p.y, p.z)) {
         ledger_add(S, p.plan, 1, e1);

@@ -21,7 +21,7 @@ from typing import Optional
 # converged warp-instructions per transport event, electron beam / photon beam: the
 # physics of a step or photon event, measured on the kernel that ran each hard event
 # inline (no parking).  The kernel that parks hard-event candidates for converged
-# passes executes 22.3 / 19.8 per event (the parking is scheduling, not physics), so
+# passes executes 22.8 / 20.4 per event (the parking is scheduling, not physics), so
 # these are the algorithmic figures
 INST_PER_EVENT_E_BEAM: Optional[float] = 19.68
 INST_PER_EVENT_PH_BEAM: Optional[float] = 18.81
