@@ -55,6 +55,15 @@ typedef int32_t gpumcd_status;
 #define GPUMCD_BEAM_PENCIL 0
 #define GPUMCD_BEAM_SQUARE 1
 #define GPUMCD_BEAM_PHASE_SPACE 2 /* primaries listed by the caller, history h taking record h mod n */
+/* Order of a phase space's records on the device (gpumcd_source.phase_space_order).
+ * GPUMCD_PHSP_BY_ENERGY groups particles of similar energy (the divergence
+ * measure §IV proposes for polyenergetic beams): the records are stably sorted
+ * by decreasing E at gpumcd_plan_open, so the histories one warp claims
+ * together start at nearby energies, and the long high-energy histories are
+ * claimed first, the short ones last.  History h then takes record h mod n of
+ * the sorted list; ties keep their listed order. */
+#define GPUMCD_PHSP_AS_LISTED 0
+#define GPUMCD_PHSP_BY_ENERGY 1
 
 /* Energy unit of the ledgers and of the dose tally: 2^-26 MeV. */
 #define GPUMCD_ENERGY_QUANTUM_MEV (1.0 / 67108864.0)
@@ -103,6 +112,9 @@ typedef struct {
      * refill_period other than 1: else GPUMCD_ERR_INVALID_ARG at run time). */
     int32_t n_phase_space;
     const double *phase_space;
+    /* GPUMCD_PHSP_AS_LISTED or GPUMCD_PHSP_BY_ENERGY for a phase space (another
+     * value: GPUMCD_ERR_INVALID_ARG); ignored by the other beams. */
+    int32_t phase_space_order;
 } gpumcd_source;
 
 /* Launch tuning; 0 in a field keeps the current value.  See gpumcd_set_launch. */

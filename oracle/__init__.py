@@ -202,6 +202,9 @@ def source(src, keep: _Keep) -> SourceC:
     ps = getattr(src, "phase_space", None)
     if ps is not None:
         a = np.ascontiguousarray(ps, dtype=np.float64).reshape(-1, 7)
+        if getattr(src, "phase_space_order", 0) == 1:
+            # records grouped by energy (§IV): decreasing E, ties in listed order
+            a = np.ascontiguousarray(a[np.argsort(-a[:, 6], kind="stable")])
         keep.refs.append(a)
         s.n_phsp = len(a)
         s.phsp = a.ctypes.data_as(_DP)

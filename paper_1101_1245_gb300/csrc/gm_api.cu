@@ -4,7 +4,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
+#include <numeric>
 #include <vector>
 
 #include "gm_common.cuh"
@@ -206,7 +208,8 @@ bool valid_source(const gpumcd_ctx *c, const gpumcd_source *s) {
     if (!s) return false;
     if (s->particle != GPUMCD_PHOTON && s->particle != GPUMCD_ELECTRON) return false;
     if (s->beam == GPUMCD_BEAM_PHASE_SPACE)  // records are checked when copied
-        return s->n_phase_space >= 1 && s->n_phase_space <= (1 << 24) && s->phase_space;
+        return s->n_phase_space >= 1 && s->n_phase_space <= (1 << 24) && s->phase_space &&
+               (s->phase_space_order == GPUMCD_PHSP_AS_LISTED || s->phase_space_order == GPUMCD_PHSP_BY_ENERGY);
     if (s->beam != GPUMCD_BEAM_PENCIL && s->beam != GPUMCD_BEAM_SQUARE) return false;
     if (!std::isfinite(s->center_cm[0]) || !std::isfinite(s->center_cm[1])) return false;
     if (s->beam == GPUMCD_BEAM_SQUARE && !(s->field_cm >= 0.0 && std::isfinite(s->field_cm))) return false;
@@ -543,10 +546,10 @@ gpumcd_status gpumcd_plan_open(gpumcd_ctx *c, int32_t phantom_id, const gpumcd_s
     }
     dev_free(c, tmp);
     if (st == GPUMCD_OK && p.beam == GPUMCD_BEAM_PHASE_SPACE) {
-        // records as float4 pairs (x, y, z, E) (ux, uy, uz, 0), direction normalised
+        // records as float4 pairs (x, y, z, E) (ux, uy, uz, 0), direction normalised;
+        // all are checked before the optional stable sort by energy
         const int32_t n = src->n_phase_space;
-        std::vector<float> h((size_t)n * 8);
-        for (int32_t i = 0; i < n && st == GPUMCD_OK; ++i) {
+        for (int32_t i = 0; i < n; ++i) {
             const double *r = src->phase_space + 7 * (size_t)i;
             bool ok = true;
             for (int a = 0; a < 7; ++a) ok = ok && std::isfinite(r[a]);
@@ -555,6 +558,17 @@ gpumcd_status gpumcd_plan_open(gpumcd_ctx *c, int32_t phantom_id, const gpumcd_s
                 st = GPUMCD_ERR_INVALID_ARG;
                 break;
             }
+        }
+        std::vector<int32_t> order((size_t)n);
+        std::iota(order.begin(), order.end(), 0);
+        if (st == GPUMCD_OK && src->phase_space_order == GPUMCD_PHSP_BY_ENERGY)
+            std::stable_sort(order.begin(), order.end(), [src](int32_t i, int32_t j) {
+                return src->phase_space[7 * (size_t)i + 6] > src->phase_space[7 * (size_t)j + 6];
+            });
+        std::vector<float> h((size_t)n * 8);
+        for (int32_t i = 0; i < n && st == GPUMCD_OK; ++i) {
+            const double *r = src->phase_space + 7 * (size_t)order[i];
+            const double nu = std::sqrt(r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
             float *o = h.data() + 8 * (size_t)i;
             o[0] = (float)r[0], o[1] = (float)r[1], o[2] = (float)r[2], o[3] = (float)r[6];
             o[4] = (float)(r[3] / nu), o[5] = (float)(r[4] / nu), o[6] = (float)(r[5] / nu), o[7] = 0.f;

@@ -97,3 +97,71 @@ def test_phase_space_validation(ctx):
         ctx.plan_close(plan)
     finally:
         ctx.destroy_phantom(pid)
+
+
+def _tied_phase_space(ph, n, seed):
+    """Records in random order whose energies take only 7 values, so that the
+    stable order of ties decides which record each history takes."""
+    src = W.point_source_phase_space(W.PHOTON, ph, n, seed=seed, field_cm=6.0)
+    rng = np.random.default_rng(seed + 1)
+    src.phase_space[:, 6] = rng.choice([0.3, 0.8, 1.25, 2.0, 3.5, 6.0, 9.0], size=n)
+    return src
+
+
+def test_grouped_by_energy_equals_the_sorted_list(ctx):
+    """GPUMCD_PHSP_BY_ENERGY is the listed records stably sorted by decreasing
+    energy: the tally, the ledger and every counter equal, bit for bit, those
+    of the same records sorted on the host (numpy's stable sort) and used as
+    listed.  997 records and 30,011 histories: a ragged last cycle."""
+    ph = W.homogeneous((24, 24, 30), 0.5, W.MAT_WATER, 1.0)
+    src = _tied_phase_space(ph, 997, 41)
+    grouped = W.Source(W.PHOTON, W.BEAM_PHASE_SPACE, phase_space=src.phase_space,
+                       phase_space_order=W.PHSP_BY_ENERGY)
+    k = np.argsort(-src.phase_space[:, 6], kind="stable")
+    listed = W.Source(W.PHOTON, W.BEAM_PHASE_SPACE, phase_space=src.phase_space[k].copy())
+    a = run_gpu(ctx, W.Plan("grouped", ph, grouped, 30_011, 9))
+    b = run_gpu(ctx, W.Plan("sorted", ph, listed, 30_011, 9))
+    assert np.array_equal(a.dose.view(np.uint64), b.dose.view(np.uint64))
+    assert np.array_equal(a.sigma.view(np.uint64), b.sigma.view(np.uint64))
+    for key in ("e_incident", "e_deposited", "e_escaped", "e_rest", "n_photon_real", "n_electron_steps"):
+        assert a.stats[key] == b.stats[key], key
+    assert a.stats["e_incident"] == _incident_quanta(listed, 30_011)
+
+
+def test_grouped_by_energy_parity(ctx):
+    """A grouped polyenergetic photon phase space against the oracle, which
+    applies the same order with its own sort: the parity bar of the other
+    phase-space tests."""
+    ph = W.z_slabs((32, 32, 48), 0.5, [(3.0, W.MAT_WATER, 1.0), (2.0, W.MAT_BONE, 1.85),
+                                       (6.0, W.MAT_LUNG, 0.26), (1e9, W.MAT_WATER, 1.0)])
+    src = W.polyenergetic_phase_space(W.PHOTON, ph, 1009, seed=23)
+    src.phase_space_order = W.PHSP_BY_ENERGY
+    plan = W.Plan("grouped_slabs", ph, src, 100_000, 37)
+    gpu = run_gpu(ctx, plan)
+    ora = run_oracle(plan)
+    assert ledger_exact(gpu.stats)
+    k = np.argsort(-src.phase_space[:, 6], kind="stable")
+    assert gpu.stats["e_incident"] == _incident_quanta(W.Source(W.PHOTON, W.BEAM_PHASE_SPACE,
+                                                                phase_space=src.phase_space[k]), 100_000)
+    do, so = ora.dose_gy(ph), ora.sigma_gy(ph)
+    mask = do > 0.1 * do.max()
+    assert mask.sum() > 100
+    assert three_sigma_pass_rate(gpu.dose, gpu.sigma, do, so, mask) >= 0.99
+    assert gpu.stats["n_photon_real"] / 100_000 == pytest.approx(ora.stats["n_photon_real"] / 100_000, rel=0.03)
+
+
+def test_phase_space_order_is_validated(ctx):
+    ph = W.homogeneous((8, 8, 8), 0.5, W.MAT_WATER, 1.0)
+    pid = ctx.create_phantom(ph)
+    try:
+        rec = np.array([[1.0, 1.0, 0.0, 0.0, 0.0, 1.0, 2.0]])
+        with pytest.raises(g.GpumcdError) as e:
+            ctx.plan_open(pid, W.Source(W.PHOTON, W.BEAM_PHASE_SPACE, phase_space=rec, phase_space_order=2), 1, 16)
+        assert e.value.status == g.ERR_INVALID_ARG
+        bad = np.array([[1.0, 1.0, 0.0, 0.0, 0.0, 1.0, 2.0], [1.0, 1.0, 0.0, 0.0, 0.0, 1.0, np.nan]])
+        with pytest.raises(g.GpumcdError) as e:  # checked before the sort
+            ctx.plan_open(pid, W.Source(W.PHOTON, W.BEAM_PHASE_SPACE, phase_space=bad,
+                                        phase_space_order=W.PHSP_BY_ENERGY), 1, 16)
+        assert e.value.status == g.ERR_INVALID_ARG
+    finally:
+        ctx.destroy_phantom(pid)

@@ -126,3 +126,24 @@ def test_point_source_phase_space_recipe():
     d = ps[:, 0:3] - src
     assert np.allclose(d / np.linalg.norm(d, axis=1, keepdims=True), ps[:, 3:6])
     assert ps[:, 6].min() >= 1.0 and ps[:, 6].max() <= 12.0 and a.max_energy == ps[:, 6].max()
+
+
+def test_polyenergetic_phase_space_recipe():
+    """Spectrum draws stay inside the bins and follow the weights; photon
+    records span the 6 MV-like spectrum, electron records 1-15 MeV; both are
+    seeded."""
+    edges, w = W.synthetic_6mv_spectrum()
+    e = W.draw_spectrum(edges, w, 200_000, seed=4)
+    assert e.min() >= edges[0] and e.max() <= edges[-1]
+    h, _ = np.histogram(e, bins=edges)
+    want = w * len(e)
+    big = want > 400
+    assert np.all(np.abs(h[big] - want[big]) <= 5 * np.sqrt(want[big]))
+    ph = W.homogeneous((40, 40, 10), 0.5, W.MAT_WATER, 1.0)
+    for particle, lo, hi in ((W.PHOTON, 0.1, 6.0), (W.ELECTRON, 1.0, 15.0)):
+        a = W.polyenergetic_phase_space(particle, ph, 3000, seed=8)
+        b = W.polyenergetic_phase_space(particle, ph, 3000, seed=8)
+        assert np.array_equal(a.phase_space, b.phase_space)
+        assert a.phase_space_order == W.PHSP_AS_LISTED
+        assert lo <= a.phase_space[:, 6].min() and a.phase_space[:, 6].max() <= hi
+        assert a.phase_space[:, 6].max() - a.phase_space[:, 6].min() > 0.8 * (hi - lo) - 1.0

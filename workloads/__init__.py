@@ -137,6 +137,7 @@ class Phantom:
 
 PHOTON, ELECTRON = 0, 1
 BEAM_PENCIL, BEAM_SQUARE, BEAM_PHASE_SPACE = 0, 1, 2
+PHSP_AS_LISTED, PHSP_BY_ENERGY = 0, 1
 
 
 @dataclasses.dataclass
@@ -151,6 +152,9 @@ class Source:
     # BEAM_PHASE_SPACE: records (n, 7) = x, y, z (cm), ux, uy, uz, E (MeV), all of
     # `particle`; history h starts as record h mod n
     phase_space: Optional[np.ndarray] = None
+    # PHSP_BY_ENERGY: the records are used stably sorted by decreasing E, so
+    # that consecutive histories start at nearby energies (§IV)
+    phase_space_order: int = PHSP_AS_LISTED
 
     @property
     def max_energy(self) -> float:
@@ -244,11 +248,12 @@ def square_field(particle: int, energy: float, phantom: Phantom, field_cm: float
 
 def point_source_phase_space(particle: int, phantom: "Phantom", n: int, seed: int,
                              source_distance_cm: float = 30.0, field_cm: float = 8.0,
-                             e_lo: float = 1.0, e_hi: float = 12.0) -> Source:
+                             e_lo: float = 1.0, e_hi: float = 12.0,
+                             energies: Optional[np.ndarray] = None) -> Source:
     """A seeded phase space standing in for a scored one: particles on the
     z = 0 face, uniform over a square field, each aimed away from a point
     source `source_distance_cm` above the face (a diverging beam), energies
-    uniform on [e_lo, e_hi] MeV."""
+    uniform on [e_lo, e_hi] MeV, or the n given `energies`."""
     rng = np.random.default_rng(seed)
     X, Y, _ = phantom.extent_cm
     x = X / 2 + (rng.random(n) - 0.5) * field_cm
@@ -256,6 +261,8 @@ def point_source_phase_space(particle: int, phantom: "Phantom", n: int, seed: in
     d = np.stack([x - X / 2, y - Y / 2, np.full(n, source_distance_cm)], axis=1)
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     e = e_lo + (e_hi - e_lo) * rng.random(n)
+    if energies is not None:
+        e = np.asarray(energies, dtype=np.float64).reshape(n)
     ps = np.column_stack([x, y, np.zeros(n), d, e])
     return Source(particle, BEAM_PHASE_SPACE, phase_space=ps)
 
@@ -277,6 +284,25 @@ def synthetic_6mv_spectrum(seed: int = 3, n_bins: int = 256, e_lo: float = 0.1,
     w = w * (1.0 + jitter * (2.0 * rng.random(n_bins) - 1.0))
     w = np.maximum(w, 0.0)
     return edges.astype(np.float64), (w / w.sum()).astype(np.float64)
+
+
+def draw_spectrum(edges: np.ndarray, weights: np.ndarray, n: int, seed: int) -> np.ndarray:
+    """n seeded energies from a histogram spectrum: a bin by its weight, then
+    uniform within the bin."""
+    rng = np.random.default_rng(seed)
+    k = rng.choice(len(weights), size=n, p=np.asarray(weights) / np.sum(weights))
+    return edges[k] + (edges[k + 1] - edges[k]) * rng.random(n)
+
+
+def polyenergetic_phase_space(particle: int, phantom: "Phantom", n: int, seed: int) -> Source:
+    """A polyenergetic phase space in random order, as a scored one would be:
+    photons from the 6 MV-like spectrum, electrons uniform on [1, 15] MeV (the
+    span of clinical electron energies), on a diverging 8 cm field."""
+    if particle == PHOTON:
+        e = draw_spectrum(*synthetic_6mv_spectrum(), n, seed + 1)
+    else:
+        e = 1.0 + 14.0 * np.random.default_rng(seed + 1).random(n)
+    return point_source_phase_space(particle, phantom, n, seed, energies=e)
 
 
 # ---------------------------------------------------------------------------
