@@ -48,7 +48,7 @@ def parse():
                          "paper's three geometries, each beam alone (Table resabsexec); ablation: "
                          "the lane refill policies on the second geometry (Table resdivred); "
                          "kerma: the photon-only mode against full transport on the c2 photon beam; "
-                         "grouping: polyenergetic phase spaces as listed vs grouped by energy")
+                         "grouping: polyenergetic phase spaces and spectra, ungrouped vs grouped by energy")
     ap.add_argument("--small", action="store_true",
                     help="ablation: 1/5 of the histories (a small case for ncu)")
     ap.add_argument("--graph", action="store_true",
@@ -624,13 +624,16 @@ def run_kerma(args):
 
 
 def run_grouping(args):
-    """Energy grouping of a polyenergetic beam (GPUMCD §IV): a phase space of
-    1e6 records in random order (6 MV-like photons, 1-15 MeV electrons) on the
-    c2 phantom (128^3 water), its records used as listed against stably sorted
-    by decreasing energy (GPUMCD_PHSP_BY_ENERGY), with the paper's timing
-    history counts.  The two orders give different (equally valid) samples of
-    the same dose; the line reports the share of voxels above 10% of the
-    maximum where they agree within 3 combined sigma."""
+    """Energy grouping of polyenergetic beams (GPUMCD §IV) on the c2 phantom
+    (128^3 water), with the paper's timing history counts, each source
+    ungrouped against grouped (energy_grouping):
+    - a phase space of 1e6 records in random order (6 MV-like photons, 1-15
+      MeV electrons), used as listed or stably sorted by decreasing energy;
+    - a 10x10 cm^2 field whose spectrum (the same energies) is sampled on the
+      device, iid or stratified over the run from the top down.
+    The two forms give different, equally valid samples of the same dose; the
+    line reports the share of voxels above 10% of the maximum where they agree
+    within 3 combined sigma."""
     import numpy as np
     import torch
 
@@ -640,53 +643,57 @@ def run_grouping(args):
     ctx = g.engine(0)
     ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     rows = []
-    for particle in (W.ELECTRON, W.PHOTON):
-        pl = W.config2(particle)
-        ph = pl.phantom
-        pid = ctx.create_phantom(ph)
-        src = W.polyenergetic_phase_space(particle, ph, 1_000_000, seed=77)
-        d = torch.zeros(ph.nvox, dtype=torch.float64, device="cuda")
-        sg = torch.zeros_like(d)
-        out = {}
-        for label, order in (("as_listed", W.PHSP_AS_LISTED), ("by_energy", W.PHSP_BY_ENERGY)):
-            src.phase_space_order = order
-            plan = ctx.plan_open(pid, src, pl.seed, 32)
+    for kind in ("phase_space", "spectrum"):
+        for particle in (W.ELECTRON, W.PHOTON):
+            pl = W.config2(particle)
+            ph = pl.phantom
+            pid = ctx.create_phantom(ph)
+            if kind == "phase_space":
+                src = W.polyenergetic_phase_space(particle, ph, 1_000_000, seed=77)
+            else:
+                src = W.polyenergetic_square(particle, ph)
+            d = torch.zeros(ph.nvox, dtype=torch.float64, device="cuda")
+            sg = torch.zeros_like(d)
+            out = {}
+            for label, grouping in (("ungrouped", W.ENERGY_UNGROUPED), ("grouped", W.ENERGY_GROUPED)):
+                src.energy_grouping = grouping
+                plan = ctx.plan_open(pid, src, pl.seed, 32)
 
-            def once():
-                ctx.plan_reset(plan, pl.seed)
-                torch.cuda.synchronize()
-                ev[0].record()
-                ctx.run([plan], [pl.n_histories])
-                st = ctx.plan_result(plan, 0.5, d.data_ptr(), sg.data_ptr())
-                ev[1].record()
-                torch.cuda.synchronize()
-                return ev[0].elapsed_time(ev[1]), st
+                def once():
+                    ctx.plan_reset(plan, pl.seed)
+                    torch.cuda.synchronize()
+                    ev[0].record()
+                    ctx.run([plan], [pl.n_histories])
+                    st = ctx.plan_result(plan, 0.5, d.data_ptr(), sg.data_ptr())
+                    ev[1].record()
+                    torch.cuda.synchronize()
+                    return ev[0].elapsed_time(ev[1]), st
 
-            for _ in range(max(1, args.warmup)):
-                once()
-            res = [once() for _ in range(args.steps)]
-            st = res[-1][1]
-            out[label] = {"ms": statistics.median(r[0] for r in res),
-                          "transport_ms": statistics.median(r[1]["transport_ms"] for r in res),
-                          "electron_steps_per_history": st["n_electron_steps"] / pl.n_histories,
-                          "ledger_exact": st["e_deposited"] + st["e_escaped"] + st["e_rest"] == st["e_incident"],
-                          "dose": d.cpu().numpy(), "sigma": sg.cpu().numpy()}
-            ctx.plan_close(plan)
-        ctx.destroy_phantom(pid)
-        a, b = out["as_listed"], out["by_energy"]
-        mask = a["dose"] > 0.1 * a["dose"].max()
-        agree = np.abs(a["dose"] - b["dose"]) <= 3.0 * np.sqrt(a["sigma"] ** 2 + b["sigma"] ** 2)
-        rows.append({"beam": "electron" if particle == W.ELECTRON else "photon",
-                     "histories": pl.n_histories, "records": 1_000_000,
-                     "transport_ms": {k: v["transport_ms"] for k, v in out.items()},
-                     "step_ms": {k: v["ms"] for k, v in out.items()},
-                     "grouped_speedup": a["transport_ms"] / b["transport_ms"],
-                     "electron_steps_per_history": {k: v["electron_steps_per_history"] for k, v in out.items()},
-                     "ledger_exact": all(v["ledger_exact"] for v in out.values()),
-                     "dose_3sigma_agreement": float(agree[mask].mean())})
+                for _ in range(max(1, args.warmup)):
+                    once()
+                res = [once() for _ in range(args.steps)]
+                st = res[-1][1]
+                out[label] = {"ms": statistics.median(r[0] for r in res),
+                              "transport_ms": statistics.median(r[1]["transport_ms"] for r in res),
+                              "electron_steps_per_history": st["n_electron_steps"] / pl.n_histories,
+                              "ledger_exact": st["e_deposited"] + st["e_escaped"] + st["e_rest"] == st["e_incident"],
+                              "dose": d.cpu().numpy(), "sigma": sg.cpu().numpy()}
+                ctx.plan_close(plan)
+            ctx.destroy_phantom(pid)
+            a, b = out["ungrouped"], out["grouped"]
+            mask = a["dose"] > 0.1 * a["dose"].max()
+            agree = np.abs(a["dose"] - b["dose"]) <= 3.0 * np.sqrt(a["sigma"] ** 2 + b["sigma"] ** 2)
+            rows.append({"source": kind, "beam": "electron" if particle == W.ELECTRON else "photon",
+                         "histories": pl.n_histories,
+                         "transport_ms": {k: v["transport_ms"] for k, v in out.items()},
+                         "step_ms": {k: v["ms"] for k, v in out.items()},
+                         "grouped_speedup": a["transport_ms"] / b["transport_ms"],
+                         "electron_steps_per_history": {k: v["electron_steps_per_history"] for k, v in out.items()},
+                         "ledger_exact": all(v["ledger_exact"] for v in out.values()),
+                         "dose_3sigma_agreement": float(agree[mask].mean())})
     ctx.close()
-    emit({"workload": "polyenergetic_phase_space_energy_grouping_c2_phantom",
-          "metric": "transport ms per beam, records as listed vs grouped by energy",
+    emit({"workload": "polyenergetic_energy_grouping_c2_phantom",
+          "metric": "transport ms per beam, ungrouped vs grouped by energy",
           "unit": "ms", "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
           "phantom": "128^3 water at 0.25 cm", "data": "synthetic", "rows": rows})
 

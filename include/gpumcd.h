@@ -55,15 +55,26 @@ typedef int32_t gpumcd_status;
 #define GPUMCD_BEAM_PENCIL 0
 #define GPUMCD_BEAM_SQUARE 1
 #define GPUMCD_BEAM_PHASE_SPACE 2 /* primaries listed by the caller, history h taking record h mod n */
-/* Order of a phase space's records on the device (gpumcd_source.phase_space_order).
- * GPUMCD_PHSP_BY_ENERGY groups particles of similar energy (the divergence
- * measure §IV proposes for polyenergetic beams): the records are stably sorted
- * by decreasing E at gpumcd_plan_open, so the histories one warp claims
- * together start at nearby energies, and the long high-energy histories are
- * claimed first, the short ones last.  History h then takes record h mod n of
- * the sorted list; ties keep their listed order. */
-#define GPUMCD_PHSP_AS_LISTED 0
-#define GPUMCD_PHSP_BY_ENERGY 1
+/* Energy grouping of a polyenergetic source (gpumcd_source.energy_grouping):
+ * particles of similar energy are started together, the divergence measure
+ * §IV proposes for polyenergetic beams.  Warps claim primaries in chunks from
+ * one cursor, so consecutive histories run side by side.  With
+ * GPUMCD_ENERGY_GROUPED:
+ * - a phase space's records are stably sorted by decreasing E at
+ *   gpumcd_plan_open; history h takes record h mod n of the sorted list (ties
+ *   keep their listed order);
+ * - a spectrum is sampled stratified within each run: of the n histories one
+ *   gpumcd_run (or gpumcd_simulate pass) gives the plan, the j-th draws the
+ *   cumulative-spectrum quantile 1 - (j + u)/n, u its own uniform draw.  Each
+ *   run is then one draw from each of n equal-probability strata, highest
+ *   energies first; the tally depends on how the histories are split into
+ *   runs (the same sizes reproduce it bit for bit);
+ * - a monoenergetic beam is unchanged.
+ * Either way the long high-energy histories are claimed first and the short
+ * ones last.  A launch holding a grouped spectral plan runs the phase-space
+ * kernel, with its restrictions. */
+#define GPUMCD_ENERGY_UNGROUPED 0
+#define GPUMCD_ENERGY_GROUPED 1
 
 /* Energy unit of the ledgers and of the dose tally: 2^-26 MeV. */
 #define GPUMCD_ENERGY_QUANTUM_MEV (1.0 / 67108864.0)
@@ -112,9 +123,9 @@ typedef struct {
      * refill_period other than 1: else GPUMCD_ERR_INVALID_ARG at run time). */
     int32_t n_phase_space;
     const double *phase_space;
-    /* GPUMCD_PHSP_AS_LISTED or GPUMCD_PHSP_BY_ENERGY for a phase space (another
-     * value: GPUMCD_ERR_INVALID_ARG); ignored by the other beams. */
-    int32_t phase_space_order;
+    /* GPUMCD_ENERGY_UNGROUPED or GPUMCD_ENERGY_GROUPED (another value:
+     * GPUMCD_ERR_INVALID_ARG at gpumcd_plan_open or gpumcd_simulate). */
+    int32_t energy_grouping;
 } gpumcd_source;
 
 /* Launch tuning; 0 in a field keeps the current value.  See gpumcd_set_launch. */

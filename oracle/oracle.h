@@ -68,6 +68,13 @@ typedef struct {
     double cx, cy, field;
     int32_t n_phsp;      /* beam 2: records */
     const double *phsp;  /* beam 2: [n_phsp][7] x, y, z (cm), ux, uy, uz, E (MeV) */
+    /* Energy grouping of a spectrum (§IV): with group = 1 and n_spec > 0, history
+     * run_begin + j (0 <= j < run_n) draws the cumulative-spectrum quantile
+     * 1 - (j + u)/run_n, u its uniform draw: one draw per equal-probability
+     * stratum, from the top of the spectrum down.  Every simulated history must
+     * lie in the run.  (A grouped phase space is sorted by the caller.) */
+    int32_t group;
+    uint64_t run_begin, run_n;
 } om_source;
 
 typedef struct {
@@ -115,6 +122,11 @@ void om_sample_brem(const om_material *m, double T, double k_c, int64_t n, uint6
 void om_sample_ms(double g1, int64_t n, uint64_t seed, double *mu_out);
 void om_sample_spectrum(int32_t n_bins, const double *edges, const double *weights, int64_t n,
                         uint64_t seed, double *e_out);
+/* Primary energies of histories [hist_begin, hist_end) of a pencil or square
+ * source, as the transport draws them (e_out[h - hist_begin]); -1 on invalid
+ * input. */
+int32_t om_primary_energies(const om_source *src, uint64_t hist_begin, uint64_t hist_end,
+                            uint64_t seed, double *e_out);
 
 /* ---- RNG: Philox4x32-10 (Salmon et al., SC'11) ---- */
 void om_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

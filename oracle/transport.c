@@ -199,16 +199,21 @@ static int spectrum_bin(int32_t n, const double *cdf, double z) {
     return lo;
 }
 
-/* Inverse-CDF draw from a histogram spectrum: choose the bin by the cumulative
- * weights, then a uniform energy inside it. */
-static double sample_spectrum(stream_t *s, int32_t n, const double *edges, const double *cdf) {
-    double z = uniform(s);
+/* Inverse CDF of a histogram spectrum at quantile z: the bin by the
+ * cumulative weights, then linear inside it (a uniform z gives a uniform energy
+ * within the bin). */
+static double spectrum_at(int32_t n, const double *edges, const double *cdf, double z) {
     int i = spectrum_bin(n, cdf, z);
     double w = cdf[i + 1] - cdf[i];
     double f = w > 0.0 ? (z - cdf[i]) / w : 0.5;
     if (f < 0.0) f = 0.0;
     if (f > 1.0) f = 1.0;
     return edges[i] + f * (edges[i + 1] - edges[i]);
+}
+
+/* Inverse-CDF draw from a histogram spectrum. */
+static double sample_spectrum(stream_t *s, int32_t n, const double *edges, const double *cdf) {
+    return spectrum_at(n, edges, cdf, uniform(s));
 }
 
 static double *spectrum_cdf(int32_t n, const double *w) {
@@ -693,7 +698,14 @@ static void make_primary(ctx_t *c, const om_source *src, const double *cdf, uint
     p->u[0] = 0.0;
     p->u[1] = 0.0;
     p->u[2] = 1.0;
-    p->E = src->n_spec > 0 ? sample_spectrum(s, src->n_spec, src->spec_edges, cdf) : src->energy;
+    if (src->n_spec > 0 && src->group) {
+        /* energy grouping (§IV): stratum h - run_begin of run_n, from the top */
+        const double u = uniform(s);
+        const double z = 1.0 - ((double)(h - src->run_begin) + u) / (double)src->run_n;
+        p->E = spectrum_at(src->n_spec, src->spec_edges, cdf, z);
+    } else {
+        p->E = src->n_spec > 0 ? sample_spectrum(s, src->n_spec, src->spec_edges, cdf) : src->energy;
+    }
     p->type = src->particle;
     p->lin = 1ull;
     p->draw = s->draw;
@@ -704,6 +716,9 @@ int32_t om_simulate(const om_material *mats, int32_t n_mat, const om_physics *ph
                     uint64_t hist_end, uint64_t seed, uint32_t flags, double *sum_e,
                     double *sum_e2, om_stats *stats) {
     if (validate(mats, n_mat, phys, ph, src) != 0 || !sum_e || !sum_e2 || !stats) return -1;
+    if (src->group && src->n_spec > 0 &&
+        (hist_begin < src->run_begin || hist_end > src->run_begin + src->run_n || src->run_n == 0))
+        return -1;
     ctx_t c;
     if (ctx_setup(&c, mats, n_mat, phys, ph, seed, flags, stats) != 0) {
         ctx_free(&c);
@@ -752,6 +767,7 @@ int32_t om_first_interaction_z(const om_material *mats, int32_t n_mat, const om_
                                const om_phantom *ph, const om_source *src, int64_t n,
                                uint64_t seed, double *z_out, uint64_t *n_fict_out) {
     if (validate(mats, n_mat, phys, ph, src) != 0 || src->particle != 0) return -1;
+    if (src->group && src->n_spec > 0 && (src->run_begin != 0 || src->run_n < (uint64_t)n)) return -1;
     om_stats st;
     memset(&st, 0, sizeof st);
     ctx_t c;
@@ -808,6 +824,26 @@ void om_sample_ms(double g1, int64_t n, uint64_t seed, double *mu_out) {
     stream_t s;
     stream_init(&s, seed, 0, 7, 0);
     for (int64_t i = 0; i < n; ++i) mu_out[i] = sample_ms_mu(&s, g1);
+}
+
+int32_t om_primary_energies(const om_source *src, uint64_t hist_begin, uint64_t hist_end,
+                            uint64_t seed, double *e_out) {
+    if (!src || !e_out || src->beam == 2 || src->n_spec < 0) return -1;
+    if (src->group && src->n_spec > 0 &&
+        (hist_begin < src->run_begin || hist_end > src->run_begin + src->run_n || src->run_n == 0))
+        return -1;
+    ctx_t c;
+    memset(&c, 0, sizeof c);
+    c.seed = seed;
+    double *cdf = src->n_spec > 0 ? spectrum_cdf(src->n_spec, src->spec_weights) : NULL;
+    for (uint64_t h = hist_begin; h < hist_end; ++h) {
+        part_t p;
+        stream_t s;
+        make_primary(&c, src, cdf, h, &p, &s);
+        e_out[h - hist_begin] = p.E;
+    }
+    free(cdf);
+    return 0;
 }
 
 void om_sample_spectrum(int32_t n_bins, const double *edges, const double *weights, int64_t n,

@@ -26,7 +26,7 @@ MAX_INFLIGHT = 2
 ENERGY_QUANTUM_MEV = 1.0 / 67108864.0
 PHOTON, ELECTRON = 0, 1
 BEAM_PENCIL, BEAM_SQUARE, BEAM_PHASE_SPACE = 0, 1, 2
-PHSP_AS_LISTED, PHSP_BY_ENERGY = 0, 1  # phase-space record order on the device
+ENERGY_UNGROUPED, ENERGY_GROUPED = 0, 1  # gpumcd_source.energy_grouping
 LAUNCH_WARP_AGGREGATE = 1
 LAUNCH_PROFILE = 2
 LAUNCH_GRAPH = 4
@@ -67,7 +67,7 @@ class Source(C.Structure):
                 ("n_spectrum", C.c_int32), ("spectrum_edges", C.POINTER(C.c_double)),
                 ("spectrum_weights", C.POINTER(C.c_double)), ("center_cm", C.c_double * 2),
                 ("field_cm", C.c_double), ("n_phase_space", C.c_int32),
-                ("phase_space", C.POINTER(C.c_double)), ("phase_space_order", C.c_int32)]
+                ("phase_space", C.POINTER(C.c_double)), ("energy_grouping", C.c_int32)]
 
 
 class Launch(C.Structure):
@@ -208,7 +208,7 @@ class _SourceBox:
             self.keep.append(a)
             self.s.n_phase_space = len(a)
             self.s.phase_space = a.ctypes.data_as(C.POINTER(C.c_double))
-            self.s.phase_space_order = getattr(src, "phase_space_order", PHSP_AS_LISTED)
+        self.s.energy_grouping = getattr(src, "energy_grouping", ENERGY_UNGROUPED)
 
 
 @dataclasses.dataclass

@@ -36,6 +36,7 @@ struct Plan {
     double energy, cx, cy, field;
     int32_t n_spec;
     uint32_t n_phsp = 0;     // phase-space records (held in `spec`)
+    bool e_group = false;    // spectrum sampled stratified per run, highest energies first
     uint64_t seed;
     uint32_t W;
     uint64_t hist_sub = 0;   // histories handed to launch sequences (numbering of the next run)
@@ -207,9 +208,9 @@ gpumcd_status set_device(gpumcd_ctx *c) {
 bool valid_source(const gpumcd_ctx *c, const gpumcd_source *s) {
     if (!s) return false;
     if (s->particle != GPUMCD_PHOTON && s->particle != GPUMCD_ELECTRON) return false;
+    if (s->energy_grouping != GPUMCD_ENERGY_UNGROUPED && s->energy_grouping != GPUMCD_ENERGY_GROUPED) return false;
     if (s->beam == GPUMCD_BEAM_PHASE_SPACE)  // records are checked when copied
-        return s->n_phase_space >= 1 && s->n_phase_space <= (1 << 24) && s->phase_space &&
-               (s->phase_space_order == GPUMCD_PHSP_AS_LISTED || s->phase_space_order == GPUMCD_PHSP_BY_ENERGY);
+        return s->n_phase_space >= 1 && s->n_phase_space <= (1 << 24) && s->phase_space;
     if (s->beam != GPUMCD_BEAM_PENCIL && s->beam != GPUMCD_BEAM_SQUARE) return false;
     if (!std::isfinite(s->center_cm[0]) || !std::isfinite(s->center_cm[1])) return false;
     if (s->beam == GPUMCD_BEAM_SQUARE && !(s->field_cm >= 0.0 && std::isfinite(s->field_cm))) return false;
@@ -524,6 +525,8 @@ gpumcd_status gpumcd_plan_open(gpumcd_ctx *c, int32_t phantom_id, const gpumcd_s
     p.cy = src->center_cm[1];
     p.field = src->field_cm;
     p.n_spec = src->n_spectrum;
+    p.e_group = src->beam != GPUMCD_BEAM_PHASE_SPACE && src->n_spectrum > 0 &&
+                src->energy_grouping == GPUMCD_ENERGY_GROUPED;
     p.seed = seed;
     p.W = n_batches;
     const uint64_t nvox = it->second.nvox;
@@ -561,7 +564,7 @@ gpumcd_status gpumcd_plan_open(gpumcd_ctx *c, int32_t phantom_id, const gpumcd_s
         }
         std::vector<int32_t> order((size_t)n);
         std::iota(order.begin(), order.end(), 0);
-        if (st == GPUMCD_OK && src->phase_space_order == GPUMCD_PHSP_BY_ENERGY)
+        if (st == GPUMCD_OK && src->energy_grouping == GPUMCD_ENERGY_GROUPED)
             std::stable_sort(order.begin(), order.end(), [src](int32_t i, int32_t j) {
                 return src->phase_space[7 * (size_t)i + 6] > src->phase_space[7 * (size_t)j + 6];
             });
@@ -854,7 +857,8 @@ gpumcd_status seq_start(gpumcd_ctx *c, Slot &sl, int32_t n_plans, const int32_t 
         d.beam = p.beam;
         d.e_src_q = (uint32_t)std::llround(p.energy / kQ);
         d.n_phsp = p.n_phsp;
-        if (p.n_phsp) A.phsp = 1;
+        d.e_group = p.e_group ? 1u : 0u;
+        if (p.n_phsp || p.e_group) A.phsp = 1;
         d.hist_base = p.hist_sub;
         d.n_hist = n_hist[i];
         const int t = p.particle;

@@ -100,7 +100,9 @@ struct __align__(16) PlanDev {
     uint32_t e_src_q, n_phsp;     // n_phsp: phase-space records (spec holds them)
     unsigned long long hist_base;  // first history of this launch
     unsigned long long n_hist;     // histories in this launch
+    uint32_t e_group, pad_g;       // e_group: spectrum stratified over this launch's histories
 };
+static_assert(sizeof(PlanDev) == 160, "the plan table in shared memory keeps its size");
 
 // Queue of particle records in global memory (overflow between launches).
 // For an input queue `cursor` counts records claimed; for an output queue it

@@ -354,7 +354,8 @@ __device__ __forceinline__ float sample_spectrum(const PlanDev &P, float z) {
 // Primary of history h of plan P (§II.C.2 initParticle): pencil or square
 // parallel beam entering through z = 0 along +z; with PHSP, a phase-space
 // plan's primary is record h mod n as listed (the first draw is still taken,
-// so the draw counter starts where the beams' does).
+// so the draw counter starts where the beams' does), and a grouped spectrum
+// is sampled stratified over the launch's histories.
 template <bool PHSP>
 __device__ __forceinline__ uint32_t make_primary(Lane &p, const PlanDev &P, uint32_t plan, uint64_t h) {
     p.hist = (uint32_t)h;
@@ -387,7 +388,15 @@ __device__ __forceinline__ uint32_t make_primary(Lane &p, const PlanDev &P, uint
     p.ux = 0.0f;
     p.uy = 0.0f;
     p.uz = 1.0f;
-    p.E = P.n_spec > 0 ? __float2uint_rn(sample_spectrum(P, u01(r.z)) * kInvQf) : P.e_src_q;
+    float zq = u01(r.z);
+    if (PHSP && P.e_group) {
+        // energy grouping (§IV): history j of the launch's n draws its quantile
+        // from stratum j, counted down from the top of the spectrum
+        const float inv_n = 1.0f / (float)P.n_hist;
+        const float j = (float)(h - P.hist_base);
+        zq = fminf(fmaxf(fmaf(-zq, inv_n, fmaf(-j, inv_n, 1.0f)), 0.0f), 1.0f);
+    }
+    p.E = P.n_spec > 0 ? __float2uint_rn(sample_spectrum(P, zq) * kInvQf) : P.e_src_q;
     p.act = true;
     return p.E;
 }

@@ -5,10 +5,12 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 import paper_1101_1245_gb300 as g
 from paper_1101_1245_gb300 import build as gbuild
+import workloads as W
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "gpumcd.h")
@@ -94,3 +96,16 @@ def test_struct_layouts_match_the_binding(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_source_marshals_energy_grouping_for_every_beam():
+    """The binding passes energy_grouping for spectra and monoenergetic beams
+    too, not only for phase spaces."""
+    edges, w = W.synthetic_6mv_spectrum(n_bins=8)
+    for src in (W.Source(W.PHOTON, W.BEAM_SQUARE, field_cm=4.0, spectrum_edges=edges, spectrum_weights=w,
+                         energy_grouping=W.ENERGY_GROUPED),
+                W.Source(W.ELECTRON, W.BEAM_PENCIL, energy=3.0, energy_grouping=W.ENERGY_GROUPED),
+                W.Source(W.PHOTON, W.BEAM_PHASE_SPACE, phase_space=np.ones((2, 7)),
+                         energy_grouping=W.ENERGY_GROUPED)):
+        assert g._SourceBox(src).s.energy_grouping == g.ENERGY_GROUPED
+    assert g._SourceBox(W.pencil(W.PHOTON, 1.0, 0.0, 0.0)).s.energy_grouping == g.ENERGY_UNGROUPED

@@ -1,6 +1,7 @@
 """Phase-space sources (GPUMCD_BEAM_PHASE_SPACE, the phase-space sources of the
 paper's outlook, §V): history h starts as record h mod n of a caller-supplied
-list.  Parity is against the oracle's own phase-space source on the same
+list.  Also the energy grouping of polyenergetic sources (§IV), which both
+phase spaces and spectra take.  Parity is against the oracle's own phase-space source on the same
 seeded records, with the bar of the other parity tests:
 - >= 99% of voxels above 10% of D_max within 3 combined sigma;
 - an exact integer ledger;
@@ -109,14 +110,14 @@ def _tied_phase_space(ph, n, seed):
 
 
 def test_grouped_by_energy_equals_the_sorted_list(ctx):
-    """GPUMCD_PHSP_BY_ENERGY is the listed records stably sorted by decreasing
+    """GPUMCD_ENERGY_GROUPED is the listed records stably sorted by decreasing
     energy: the tally, the ledger and every counter equal, bit for bit, those
     of the same records sorted on the host (numpy's stable sort) and used as
     listed.  997 records and 30,011 histories: a ragged last cycle."""
     ph = W.homogeneous((24, 24, 30), 0.5, W.MAT_WATER, 1.0)
     src = _tied_phase_space(ph, 997, 41)
     grouped = W.Source(W.PHOTON, W.BEAM_PHASE_SPACE, phase_space=src.phase_space,
-                       phase_space_order=W.PHSP_BY_ENERGY)
+                       energy_grouping=W.ENERGY_GROUPED)
     k = np.argsort(-src.phase_space[:, 6], kind="stable")
     listed = W.Source(W.PHOTON, W.BEAM_PHASE_SPACE, phase_space=src.phase_space[k].copy())
     a = run_gpu(ctx, W.Plan("grouped", ph, grouped, 30_011, 9))
@@ -135,7 +136,7 @@ def test_grouped_by_energy_parity(ctx):
     ph = W.z_slabs((32, 32, 48), 0.5, [(3.0, W.MAT_WATER, 1.0), (2.0, W.MAT_BONE, 1.85),
                                        (6.0, W.MAT_LUNG, 0.26), (1e9, W.MAT_WATER, 1.0)])
     src = W.polyenergetic_phase_space(W.PHOTON, ph, 1009, seed=23)
-    src.phase_space_order = W.PHSP_BY_ENERGY
+    src.energy_grouping = W.ENERGY_GROUPED
     plan = W.Plan("grouped_slabs", ph, src, 100_000, 37)
     gpu = run_gpu(ctx, plan)
     ora = run_oracle(plan)
@@ -150,18 +151,90 @@ def test_grouped_by_energy_parity(ctx):
     assert gpu.stats["n_photon_real"] / 100_000 == pytest.approx(ora.stats["n_photon_real"] / 100_000, rel=0.03)
 
 
-def test_phase_space_order_is_validated(ctx):
+def test_energy_grouping_is_validated(ctx):
     ph = W.homogeneous((8, 8, 8), 0.5, W.MAT_WATER, 1.0)
     pid = ctx.create_phantom(ph)
     try:
         rec = np.array([[1.0, 1.0, 0.0, 0.0, 0.0, 1.0, 2.0]])
         with pytest.raises(g.GpumcdError) as e:
-            ctx.plan_open(pid, W.Source(W.PHOTON, W.BEAM_PHASE_SPACE, phase_space=rec, phase_space_order=2), 1, 16)
+            ctx.plan_open(pid, W.Source(W.PHOTON, W.BEAM_PHASE_SPACE, phase_space=rec, energy_grouping=2), 1, 16)
         assert e.value.status == g.ERR_INVALID_ARG
         bad = np.array([[1.0, 1.0, 0.0, 0.0, 0.0, 1.0, 2.0], [1.0, 1.0, 0.0, 0.0, 0.0, 1.0, np.nan]])
         with pytest.raises(g.GpumcdError) as e:  # checked before the sort
             ctx.plan_open(pid, W.Source(W.PHOTON, W.BEAM_PHASE_SPACE, phase_space=bad,
-                                        phase_space_order=W.PHSP_BY_ENERGY), 1, 16)
+                                        energy_grouping=W.ENERGY_GROUPED), 1, 16)
         assert e.value.status == g.ERR_INVALID_ARG
     finally:
+        ctx.destroy_phantom(pid)
+
+
+def _mean_energy(edges, w):
+    return float(np.sum(np.asarray(w) * 0.5 * (edges[:-1] + edges[1:])) / np.sum(w))
+
+
+def test_grouped_spectrum_parity_and_strata(ctx):
+    """A grouped 6 MV-like photon spectrum (one draw per stratum of each run,
+    highest energies first) against the oracle's grouped run: the dose within
+    3 sigma, an exact ledger, and an incident energy that only stratification
+    gives - within the spectrum's width of n times its mean energy on both
+    sides, where iid draws scatter by ~400 MeV at this n."""
+    edges, w = W.synthetic_6mv_spectrum()
+    ph = W.z_slabs((32, 32, 48), 0.5, [(3.0, W.MAT_WATER, 1.0), (2.0, W.MAT_BONE, 1.85),
+                                       (6.0, W.MAT_LUNG, 0.26), (1e9, W.MAT_WATER, 1.0)])
+    src = W.Source(W.PHOTON, W.BEAM_SQUARE, center_cm=(8.0, 8.0), field_cm=8.0, spectrum_edges=edges,
+                   spectrum_weights=w, energy_grouping=W.ENERGY_GROUPED)
+    n = 100_000
+    plan = W.Plan("grouped_spectrum", ph, src, n, 43)
+    gpu = run_gpu(ctx, plan)
+    ora = run_oracle(plan)
+    assert ledger_exact(gpu.stats)
+    width = float(edges[-1] - edges[0])
+    want = n * _mean_energy(edges, w)
+    assert abs(gpu.stats["e_incident"] * Q - want) <= 2.0 * width
+    assert abs(ora.stats["e_incident"] - want) <= width + 1e-6
+    do, so = ora.dose_gy(ph), ora.sigma_gy(ph)
+    mask = do > 0.1 * do.max()
+    assert mask.sum() > 100
+    assert three_sigma_pass_rate(gpu.dose, gpu.sigma, do, so, mask) >= 0.99
+    assert gpu.stats["n_photon_real"] / n == pytest.approx(ora.stats["n_photon_real"] / n, rel=0.03)
+
+
+def test_grouping_leaves_a_monoenergetic_beam_unchanged(ctx):
+    """A monoenergetic beam has nothing to group: its tallies are bit-identical
+    with and without the flag (the production kernel runs both)."""
+    ph = W.homogeneous((16, 16, 24), 0.5, W.MAT_WATER, 1.0)
+    a = run_gpu(ctx, W.Plan("mono", ph, W.pencil(W.ELECTRON, 6.0, 4.0, 4.0), 20_000, 3))
+    src = W.pencil(W.ELECTRON, 6.0, 4.0, 4.0)
+    src.energy_grouping = W.ENERGY_GROUPED
+    b = run_gpu(ctx, W.Plan("mono_grouped", ph, src, 20_000, 3))
+    assert np.array_equal(a.dose.view(np.uint64), b.dose.view(np.uint64))
+    assert a.stats["n_electron_steps"] == b.stats["n_electron_steps"]
+
+
+def test_grouped_spectrum_runs_the_phase_space_kernel(ctx):
+    """A grouped spectral plan is drawn by the phase-space instantiation, so the
+    photon-only flag (which has no such instantiation) is refused for it, and
+    accepted again for the same spectrum ungrouped."""
+    edges, w = W.synthetic_6mv_spectrum(n_bins=32)
+    ph = W.homogeneous((8, 8, 8), 0.5, W.MAT_WATER, 1.0)
+    pid = ctx.create_phantom(ph)
+    try:
+        grouped = W.Source(W.PHOTON, W.BEAM_PENCIL, center_cm=(2.0, 2.0), spectrum_edges=edges,
+                           spectrum_weights=w, energy_grouping=W.ENERGY_GROUPED)
+        plain = W.Source(W.PHOTON, W.BEAM_PENCIL, center_cm=(2.0, 2.0), spectrum_edges=edges,
+                         spectrum_weights=w)
+        pg = ctx.plan_open(pid, grouped, 1, 16)
+        pp = ctx.plan_open(pid, plain, 1, 16)
+        ctx.set_launch(flags=g.LAUNCH_KERMA)
+        with pytest.raises(g.GpumcdError) as e:
+            ctx.run([pg], [64])
+        assert e.value.status == g.ERR_INVALID_ARG
+        ctx.run([pp], [64])
+        ctx.set_launch(flags=0)
+        ctx.run([pg], [64])
+        assert ctx.plan_result(pg, 0.5)["histories"] == 64
+        ctx.plan_close(pg)
+        ctx.plan_close(pp)
+    finally:
+        ctx.set_launch(flags=0)
         ctx.destroy_phantom(pid)

@@ -251,7 +251,7 @@ def test_phase_space_grouped_by_energy_takes_the_records_in_decreasing_energy():
     rows = sorted(range(9), key=lambda i: -src.phase_space[i, 6])
     n = 67
     grouped = W.Source(W.ELECTRON, W.BEAM_PHASE_SPACE, phase_space=src.phase_space,
-                       phase_space_order=W.PHSP_BY_ENERGY)
+                       energy_grouping=W.ENERGY_GROUPED)
     listed = W.Source(W.ELECTRON, W.BEAM_PHASE_SPACE, phase_space=src.phase_space[rows])
     a = oracle.simulate(W.MATERIALS, P, ph, grouped, n, 6)
     b = oracle.simulate(W.MATERIALS, P, ph, listed, n, 6)
@@ -260,3 +260,53 @@ def test_phase_space_grouped_by_energy_takes_the_records_in_decreasing_energy():
     assert np.array_equal(a.sum_e, b.sum_e) and np.array_equal(a.sum_e2, b.sum_e2)
     c = oracle.simulate(W.MATERIALS, P, ph, src, n, 6)  # as listed: another sample
     assert not np.array_equal(a.sum_e, c.sum_e)
+
+
+def _strata_deviation(e, edges, w):
+    """Largest |#(E < edge_i) - n * CDF(edge_i)| over the spectrum's edges."""
+    cdf = np.concatenate([[0.0], np.cumsum(w) / np.sum(w)])
+    counts = np.searchsorted(np.sort(e), edges, side="left")
+    return float(np.max(np.abs(counts - len(e) * cdf)))
+
+
+@pytest.mark.parametrize("run", [(0, 2000), (700, 1500)])
+def test_grouped_spectrum_draws_one_energy_per_stratum(run):
+    """A grouped spectrum (§IV's grouping of similar energies) draws, for the
+    j-th history of a run of n, the quantile 1 - (j + u)/n.  Pinned by what
+    that fixes: energies never rise along the run, and for every bin edge the
+    number of energies below it is n * CDF(edge) to within one (a stratum
+    straddles the edge); iid draws miss that bound by tens."""
+    edges, w = W.synthetic_6mv_spectrum(n_bins=64)
+    src = W.Source(W.PHOTON, W.BEAM_PENCIL, center_cm=(1.0, 1.0), spectrum_edges=edges,
+                   spectrum_weights=w, energy_grouping=W.ENERGY_GROUPED)
+    h0, n = run
+    e = oracle.primary_energies(src, h0, h0 + n, seed=12, run=run)
+    assert np.all(np.diff(e) <= 0.0)
+    assert e.min() >= edges[0] and e.max() <= edges[-1]
+    assert _strata_deviation(e, edges, w) <= 1.0 + 1e-9
+    # inverting the CDF recovers each history's uniform: in [0, 1], mean 1/2
+    cdf = np.concatenate([[0.0], np.cumsum(w) / np.sum(w)])
+    u = (1.0 - np.interp(e, edges, cdf)) * n - np.arange(n)
+    assert u.min() >= -1e-6 and u.max() <= 1.0 + 1e-6
+    assert abs(u.mean() - 0.5) < 0.03
+    src.energy_grouping = W.ENERGY_UNGROUPED
+    iid = oracle.primary_energies(src, h0, h0 + n, seed=12)
+    assert _strata_deviation(iid, edges, w) > 5.0
+    # half a run is the top half of the spectrum: a run is one stratified whole
+    src.energy_grouping = W.ENERGY_GROUPED
+    top = oracle.primary_energies(src, h0, h0 + n // 2, seed=12, run=run)
+    assert np.array_equal(top, e[: n // 2])
+    median = np.interp(0.5, cdf, edges)
+    assert top.min() >= median - 1e-9
+
+
+def test_grouped_spectrum_rejects_histories_outside_the_run():
+    edges, w = W.synthetic_6mv_spectrum(n_bins=16)
+    src = W.Source(W.PHOTON, W.BEAM_PENCIL, spectrum_edges=edges, spectrum_weights=w,
+                   energy_grouping=W.ENERGY_GROUPED)
+    with pytest.raises(RuntimeError):
+        oracle.primary_energies(src, 0, 100, seed=1, run=(10, 200))
+    with pytest.raises(RuntimeError):
+        oracle.primary_energies(src, 150, 250, seed=1, run=(0, 200))
+    mono = W.Source(W.PHOTON, W.BEAM_PENCIL, energy=2.0, energy_grouping=W.ENERGY_GROUPED)
+    assert np.all(oracle.primary_energies(mono, 0, 50, seed=1, run=(0, 10)) == 2.0)  # unchanged

@@ -144,6 +144,6 @@ def test_polyenergetic_phase_space_recipe():
         a = W.polyenergetic_phase_space(particle, ph, 3000, seed=8)
         b = W.polyenergetic_phase_space(particle, ph, 3000, seed=8)
         assert np.array_equal(a.phase_space, b.phase_space)
-        assert a.phase_space_order == W.PHSP_AS_LISTED
+        assert a.energy_grouping == W.ENERGY_UNGROUPED
         assert lo <= a.phase_space[:, 6].min() and a.phase_space[:, 6].max() <= hi
         assert a.phase_space[:, 6].max() - a.phase_space[:, 6].min() > 0.8 * (hi - lo) - 1.0

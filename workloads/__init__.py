@@ -137,7 +137,7 @@ class Phantom:
 
 PHOTON, ELECTRON = 0, 1
 BEAM_PENCIL, BEAM_SQUARE, BEAM_PHASE_SPACE = 0, 1, 2
-PHSP_AS_LISTED, PHSP_BY_ENERGY = 0, 1
+ENERGY_UNGROUPED, ENERGY_GROUPED = 0, 1
 
 
 @dataclasses.dataclass
@@ -152,9 +152,9 @@ class Source:
     # BEAM_PHASE_SPACE: records (n, 7) = x, y, z (cm), ux, uy, uz, E (MeV), all of
     # `particle`; history h starts as record h mod n
     phase_space: Optional[np.ndarray] = None
-    # PHSP_BY_ENERGY: the records are used stably sorted by decreasing E, so
+    # ENERGY_GROUPED: the records are used stably sorted by decreasing E, so
     # that consecutive histories start at nearby energies (§IV)
-    phase_space_order: int = PHSP_AS_LISTED
+    energy_grouping: int = ENERGY_UNGROUPED
 
     @property
     def max_energy(self) -> float:
@@ -292,6 +292,18 @@ def draw_spectrum(edges: np.ndarray, weights: np.ndarray, n: int, seed: int) -> 
     rng = np.random.default_rng(seed)
     k = rng.choice(len(weights), size=n, p=np.asarray(weights) / np.sum(weights))
     return edges[k] + (edges[k + 1] - edges[k]) * rng.random(n)
+
+
+def polyenergetic_square(particle: int, phantom: "Phantom", field_cm: float = 10.0) -> Source:
+    """A square field with a spectrum sampled on the device: photons from the
+    6 MV-like spectrum, electrons flat on [1, 15] MeV (14 bins)."""
+    if particle == PHOTON:
+        edges, w = synthetic_6mv_spectrum()
+    else:
+        edges, w = np.linspace(1.0, 15.0, 15), np.full(14, 1.0 / 14)
+    X, Y, _ = phantom.extent_cm
+    return Source(particle, BEAM_SQUARE, center_cm=(X / 2, Y / 2), field_cm=field_cm,
+                  spectrum_edges=edges, spectrum_weights=w)
 
 
 def polyenergetic_phase_space(particle: int, phantom: "Phantom", n: int, seed: int) -> Source:
