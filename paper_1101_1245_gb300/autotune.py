@@ -7,14 +7,16 @@ speed but never its result: every particle's random stream and energy ledger
 are independent of scheduling, so the tally is bit-identical for any setting.
 The tuner therefore times real plans - a sample of the workload at reduced
 history counts - under candidate settings by coordinate descent and keeps the
-fastest.
+fastest.  A setting the library refuses for the sampled plans (the
+phase-space kernel, which also draws grouped spectra, runs at most two CTAs
+per SM) is recorded as a refused trial and skipped.
 """
 from __future__ import annotations
 
 import statistics
 from typing import Dict, List, Sequence, Tuple
 
-from . import Context
+from . import ERR_INVALID_ARG, Context, GpumcdError
 
 # (block_threads, blocks_per_sm) shapes with a kernel variant behind them
 SHAPES: List[Tuple[int, int]] = [(512, 2), (384, 2), (256, 3), (512, 1)]
@@ -35,11 +37,23 @@ def _time(ctx: Context, plans: Sequence[int], hist: Sequence[int], reps: int) ->
     return statistics.median(ts)
 
 
+def _try(ctx: Context, plans, hist, reps: int):
+    """Transport ms under the launch set on ctx, or None if the library refuses
+    that launch for these plans."""
+    try:
+        return _time(ctx, plans, hist, reps)
+    except GpumcdError as e:
+        if e.status != ERR_INVALID_ARG:
+            raise
+        return None
+
+
 def autotune(ctx: Context, samples: Sequence[Tuple[int, object, int]], reps: int = 3,
              n_batches: int = 16) -> dict:
     """samples: (phantom_id, workload Source, histories) triples run together in
     one batched launch per trial.  Leaves the best launch on ctx and returns it
-    with the trial timings (ms of transport per trial)."""
+    with the trial timings (ms of transport per trial; None for a launch the
+    library refused)."""
     plans = [ctx.plan_open(pid, src, 1, n_batches) for pid, src, _ in samples]
     hist = [n for _, _, n in samples]
     base = ctx.get_launch()
@@ -51,10 +65,13 @@ def autotune(ctx: Context, samples: Sequence[Tuple[int, object, int]], reps: int
             cand = dict(best, block_threads=bt, blocks_per_sm=bps,
                         stack_capacity=max(best["stack_capacity"], 512))
             ctx.set_launch(**cand)
-            ms = _time(ctx, plans, hist, reps)
+            ms = _try(ctx, plans, hist, reps)
             trials.append((dict(block_threads=bt, blocks_per_sm=bps), ms))
-            if best_ms is None or ms < best_ms:
+            if ms is not None and (best_ms is None or ms < best_ms):
                 best, best_ms = cand, ms
+        if best_ms is None:
+            ctx.set_launch(**base)
+            raise GpumcdError(ERR_INVALID_ARG, "autotune: every launch shape refused")
         for knob, values in KNOBS.items():
             for v in values:
                 if v == best[knob]:
@@ -63,9 +80,9 @@ def autotune(ctx: Context, samples: Sequence[Tuple[int, object, int]], reps: int
                 if cand["switch_high"] > cand["stack_capacity"]:
                     continue
                 ctx.set_launch(**cand)
-                ms = _time(ctx, plans, hist, reps)
+                ms = _try(ctx, plans, hist, reps)
                 trials.append(({knob: v}, ms))
-                if ms < best_ms:
+                if ms is not None and ms < best_ms:
                     best, best_ms = cand, ms
         ctx.set_launch(**best)
     finally:
