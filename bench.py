@@ -50,7 +50,7 @@ def parse():
                          "kerma: the photon-only mode against full transport on the c2 photon beam; "
                          "grouping: polyenergetic phase spaces and spectra, ungrouped vs grouped by energy")
     ap.add_argument("--small", action="store_true",
-                    help="ablation: 1/5 of the histories (a small case for ncu)")
+                    help="ablation, grouping: 1/5 of the histories (a small case for ncu)")
     ap.add_argument("--graph", action="store_true",
                     help="launch each sequence's first launch from a captured CUDA graph")
     ap.add_argument("--requests", type=int, default=1000, help="served: number of requests")
@@ -646,6 +646,8 @@ def run_grouping(args):
     for kind in ("phase_space", "spectrum"):
         for particle in (W.ELECTRON, W.PHOTON):
             pl = W.config2(particle)
+            if args.small:
+                pl.n_histories //= 5
             ph = pl.phantom
             pid = ctx.create_phantom(ph)
             if kind == "phase_space":
