@@ -131,6 +131,9 @@ def lib() -> C.CDLL:
             L.om_primary_energies.restype = C.c_int32
             L.om_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                            C.POINTER(C.c_uint32)]
+            L.om_rotate.argtypes = [_DP, d, d, _DP]
+            L.om_compton_kinematics.argtypes = [d, _DP, d, d, d, _DP, _DP, _DP]
+            L.om_moller_kinematics.argtypes = [d, d, _DP]
             L.om_simulate.argtypes = [_MP, C.c_int32, C.POINTER(Physics), C.POINTER(PhantomC),
                                       C.POINTER(SourceC), C.c_uint64, C.c_uint64, C.c_uint64,
                                       C.c_uint32, _DP, _DP, C.POINTER(Stats)]
@@ -409,3 +412,33 @@ def sample(kind: str, n: int, seed: int, *params):
     else:
         raise ValueError(kind)
     return out
+
+
+def rotate(u, cos_t: float, phi: float) -> np.ndarray:
+    """The transport's rotation of unit vector u by polar angle acos(cos_t)
+    and azimuth phi."""
+    L = lib()
+    a = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros(3, dtype=np.float64)
+    L.om_rotate(a.ctypes.data_as(_DP), cos_t, phi, out.ctypes.data_as(_DP))
+    return out
+
+
+def compton_kinematics(E: float, u, cos_t: float, eps: float, phi: float):
+    """The transport's Compton kinematics: (photon direction, recoil electron
+    direction, E', T)."""
+    L = lib()
+    a = np.ascontiguousarray(u, dtype=np.float64)
+    u1, ue, o = np.zeros(3), np.zeros(3), np.zeros(2)
+    L.om_compton_kinematics(E, a.ctypes.data_as(_DP), cos_t, eps, phi, u1.ctypes.data_as(_DP),
+                            ue.ctypes.data_as(_DP), o.ctypes.data_as(_DP))
+    return u1, ue, float(o[0]), float(o[1])
+
+
+def moller_kinematics(T: float, eps: float):
+    """The transport's Moller kinematics: (T_knock-on, T_scattered,
+    cos_knock-on, cos_scattered)."""
+    L = lib()
+    o = np.zeros(4)
+    L.om_moller_kinematics(T, eps, o.ctypes.data_as(_DP))
+    return tuple(float(x) for x in o)

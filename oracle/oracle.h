@@ -128,6 +128,18 @@ void om_sample_spectrum(int32_t n_bins, const double *edges, const double *weigh
 int32_t om_primary_energies(const om_source *src, uint64_t hist_begin, uint64_t hist_end,
                             uint64_t seed, double *e_out);
 
+/* ---- kinematics the transport uses, for the pins ---- */
+/* out = u rotated by polar angle acos(c) and azimuth phi (a unit vector). */
+void om_rotate(const double u[3], double c, double phi, double out[3]);
+/* Compton scattering of a photon of energy E along u at (cos_t, phi) with
+ * k'/k = eps: u1_out the photon's new direction, ue_out the recoil electron's,
+ * out = {E', T}. */
+void om_compton_kinematics(double E, const double u[3], double cos_t, double eps, double phi,
+                           double u1_out[3], double ue_out[3], double out[2]);
+/* Moller event of an electron of kinetic energy T with knock-on fraction eps:
+ * out = {T_knock-on, T_scattered, cos_knock-on, cos_scattered}. */
+void om_moller_kinematics(double T, double eps, double out[4]);
+
 /* ---- RNG: Philox4x32-10 (Salmon et al., SC'11) ---- */
 void om_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 

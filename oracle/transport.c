@@ -90,6 +90,49 @@ static void rotate(double u[3], double c, double phi) {
     u[2] /= n;
 }
 
+void om_rotate(const double u[3], double c, double phi, double out[3]) {
+    out[0] = u[0];
+    out[1] = u[1];
+    out[2] = u[2];
+    rotate(out, c, phi);
+}
+
+/* Compton kinematics (§II.A): the photon leaves along u rotated by (cos_t, phi)
+ * with energy eps E; the recoil electron takes T = E - eps E along the momentum
+ * balance E u - E' u'. */
+static void compton_kinematics(double E, const double u[3], double cos_t, double eps, double phi,
+                               double u1[3], double ue[3], double *E1, double *T) {
+    *E1 = eps * E;
+    *T = E - *E1;
+    u1[0] = u[0];
+    u1[1] = u[1];
+    u1[2] = u[2];
+    rotate(u1, cos_t, phi);
+    for (int a = 0; a < 3; ++a) ue[a] = E * u[a] - *E1 * u1[a];
+    double n = sqrt(ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2]);
+    if (n > 0.0)
+        for (int a = 0; a < 3; ++a) ue[a] /= n;
+}
+
+void om_compton_kinematics(double E, const double u[3], double cos_t, double eps, double phi,
+                           double u1_out[3], double ue_out[3], double out[2]) {
+    compton_kinematics(E, u, cos_t, eps, phi, u1_out, ue_out, &out[0], &out[1]);
+}
+
+/* Moller kinematics (§II.B.1): a knock-on of kinetic energy eps T and the
+ * scattered electron with the rest, at the polar angles of a free two-body
+ * collision, cos = sqrt(T'(T + 2mc^2)/(T (T' + 2mc^2))) for each. */
+static void moller_kinematics(double T, double eps, double *Tk, double *Tp, double *ck, double *cp) {
+    *Tk = eps * T;
+    *Tp = T - *Tk;
+    *ck = sqrt(*Tk * (T + 2.0 * OM_MC2) / (T * (*Tk + 2.0 * OM_MC2)));
+    *cp = sqrt(*Tp * (T + 2.0 * OM_MC2) / (T * (*Tp + 2.0 * OM_MC2)));
+}
+
+void om_moller_kinematics(double T, double eps, double out[4]) {
+    moller_kinematics(T, eps, &out[0], &out[1], &out[2], &out[3]);
+}
+
 /* ------------------------------------------------------------------------
  * Samplers (exact).
  * ------------------------------------------------------------------------ */
@@ -460,15 +503,8 @@ static void transport_photon(ctx_t *c, part_t *p) {
             double cs, eps;
             sample_kn(&s, p->E / OM_MC2, &cs, &eps);
             double phi = 2.0 * OM_PI * uniform(&s);
-            double E1 = eps * p->E;
-            double T = p->E - E1;
-            double u1[3] = {p->u[0], p->u[1], p->u[2]};
-            rotate(u1, cs, phi);
-            double pe[3];
-            for (int a = 0; a < 3; ++a) pe[a] = p->E * p->u[a] - E1 * u1[a];
-            double n = sqrt(pe[0] * pe[0] + pe[1] * pe[1] + pe[2] * pe[2]);
-            if (n > 0.0)
-                for (int a = 0; a < 3; ++a) pe[a] /= n;
+            double E1, T, u1[3], pe[3];
+            compton_kinematics(p->E, p->u, cs, eps, phi, u1, pe, &E1, &T);
             emit_electron(c, p->x, pe, T, p, 0);
             p->E = E1;
             memcpy(p->u, u1, sizeof u1);
@@ -594,9 +630,8 @@ static void transport_electron(ctx_t *c, part_t *p) {
         if (moller) {
             c->st->n_moller++;
             double eps = sample_moller(&s, T1, P->t_c);
-            double Tk = eps * T1, Tp = T1 - Tk;
-            double ck = sqrt(Tk * (T1 + 2.0 * OM_MC2) / (T1 * (Tk + 2.0 * OM_MC2)));
-            double cp = sqrt(Tp * (T1 + 2.0 * OM_MC2) / (T1 * (Tp + 2.0 * OM_MC2)));
+            double Tk, Tp, ck, cp;
+            moller_kinematics(T1, eps, &Tk, &Tp, &ck, &cp);
             double phi = 2.0 * OM_PI * uniform(&s);
             double uk[3] = {p->u[0], p->u[1], p->u[2]};
             rotate(uk, ck, phi);

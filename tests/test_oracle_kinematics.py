@@ -1,0 +1,196 @@
+"""Pins for the parts of the oracle that the sampler and cross-section pins do
+not reach: the magnitudes of the pair and bremsstrahlung forms (against the
+textbook radiation length), the direction rotation and the Compton and Moller
+kinematics (against geometry and momentum conservation), the electron
+Woodcock acceptance (invariance to a raised majorant, GPUMCD §II.B.3) and the
+history-by-history uncertainty estimator (§II.D) against the spread of
+independent runs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from tests._stats import three_sigma_pass_rate
+from tests.conftest import host_cores
+
+MC2 = 0.51099895
+P = W.DEFAULT_PHYSICS
+
+# Radiation lengths X0 in g/cm^2 (Particle Data Group, atomic and nuclear
+# properties of materials).  In complete screening the pair cross-section
+# tends to (7/9)/X0 and the radiative stopping power to E/X0; the simplified
+# Bethe-Heitler forms (no Coulomb correction, Z(Z+1) for the atomic electrons)
+# land within a few percent of these for light elements.
+X0_PDG = {
+    "water": (W.WATER, 36.08),
+    "carbon": (W.Material("carbon", (("C", 1.0),), 78.0, 2.0), 42.70),
+    "nitrogen": (W.Material("nitrogen", (("N", 1.0),), 82.0, 1.0), 37.99),
+    "oxygen": (W.Material("oxygen", (("O", 1.0),), 95.0, 1.0), 34.24),
+}
+
+
+@pytest.mark.parametrize("name", sorted(X0_PDG))
+def test_pair_high_energy_limit_is_seven_ninths_of_inverse_radiation_length(name):
+    """GPUMCD §II.A pair production: (9/7) mu_pp/rho -> 1/X0 as E -> infinity.
+    A dropped factor 4, 9/7 for 7/9, Z^2 for Z(Z+1) or a wrong screening
+    logarithm each move this by far more than the 6% allowed."""
+    mat, x0 = X0_PDG[name]
+    mu_inf = oracle.xs("mu_pair", mat, 1e9)
+    assert (9.0 / 7.0) * mu_inf * x0 == pytest.approx(1.0, abs=0.06)
+
+
+@pytest.mark.parametrize("name", sorted(X0_PDG))
+def test_radiative_stopping_power_tends_to_energy_over_radiation_length(name):
+    """GPUMCD §II.B.1 bremsstrahlung: S_rad/rho -> E/X0 at high energy."""
+    mat, x0 = X0_PDG[name]
+    T = 1e6
+    assert oracle.xs("s_rad", mat, T) / (T + MC2) * x0 == pytest.approx(1.0, abs=0.06)
+
+
+def test_pair_and_brem_share_the_complete_screening_constant():
+    """Per element, (9/7) sigma_pp(inf) / (S_rad / E)(inf) = (ln - 1/42)/(ln + 1/18)
+    with ln = ln(183 Z^-1/3): both forms carry the same 4 alpha re^2 Z(Z+1)."""
+    for Z, sym in ((1, "H"), (6, "C"), (8, "O"), (20, "Ca")):
+        mat = W.Material(sym, ((sym, 1.0),), 100.0, 1.0)
+        ln = math.log(183.0 * Z ** (-1.0 / 3.0))
+        T = 1e9
+        ratio = (9.0 / 7.0) * oracle.xs("mu_pair", mat, 1e12) / (oracle.xs("s_rad", mat, T) / (T + MC2))
+        assert ratio == pytest.approx((ln - 1.0 / 42.0) / (ln + 1.0 / 18.0), rel=1e-6)
+
+
+def _unit(rng, n):
+    v = rng.normal(size=(n, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def _directions(rng):
+    special = np.array([[0, 0, 1.0], [0, 0, -1.0], [1.0, 0, 0], [0, 1.0, 0],
+                        [1e-7, 0, 1.0], [0, -1e-6, -1.0]])
+    special /= np.linalg.norm(special, axis=1, keepdims=True)
+    return np.vstack([special, _unit(rng, 60)])
+
+
+def test_rotation_sets_the_polar_angle_and_opposite_azimuths_stay_in_one_plane():
+    """The rotation every interaction uses: u . u' = cos theta, |u'| = 1; the
+    azimuths phi and phi + pi put u'(phi) + u'(phi + pi) = 2 cos theta u (one
+    plane with u), and phi + pi/2 is perpendicular about u.  A sign slip in
+    any component breaks one of these."""
+    rng = np.random.default_rng(3)
+    for u in _directions(rng):
+        for c in (-1.0, -0.7, -0.1, 0.0, 0.3, 0.9, 1.0):
+            for phi in rng.uniform(0.0, 2.0 * math.pi, 5):
+                a = oracle.rotate(u, c, phi)
+                b = oracle.rotate(u, c, phi + math.pi)
+                q = oracle.rotate(u, c, phi + 0.5 * math.pi)
+                assert np.linalg.norm(a) == pytest.approx(1.0, abs=1e-12)
+                assert float(u @ a) == pytest.approx(c, abs=1e-12)
+                assert float(u @ q) == pytest.approx(c, abs=1e-12)
+                np.testing.assert_allclose(a + b, 2.0 * c * u, atol=1e-12)
+                assert float((a - c * u) @ (q - c * u)) == pytest.approx(0.0, abs=1e-12)
+
+
+def test_rotation_azimuth_is_uniform_around_the_axis():
+    """Uniform phi gives a perpendicular component whose mean vanishes and
+    whose covariance is isotropic in the plane normal to u."""
+    rng = np.random.default_rng(4)
+    u = _unit(rng, 1)[0]
+    s2 = 1.0 - 0.2 ** 2
+    perp = np.array([oracle.rotate(u, 0.2, phi) - 0.2 * u for phi in rng.uniform(0, 2 * math.pi, 4000)])
+    assert np.abs(perp.mean(axis=0)).max() < 4.0 * math.sqrt(s2 / 2 / 4000)
+    cov = perp.T @ perp / len(perp)
+    proj = np.eye(3) - np.outer(u, u)
+    np.testing.assert_allclose(cov, 0.5 * s2 * proj, atol=0.03)
+
+
+@pytest.mark.parametrize("E", [0.05, 0.6, 3.0, 15.0])
+def test_compton_kinematics_conserve_energy_and_momentum(E):
+    """GPUMCD §II.A Compton: for sampled (cos theta, k'/k) the photon and the
+    recoil electron carry E u = E' u' + p_e u_e with p_e = sqrt(T (T + 2 mc^2)),
+    T = E - E'.  That holds only for k'/k = 1/(1 + k(1 - cos theta)), so it
+    also pins the sampler's pairing of angle and energy."""
+    rng = np.random.default_rng(int(E * 100))
+    cos, eps = oracle.sample("kn", 400, 17, E / MC2)
+    for u, c, e, phi in zip(_unit(rng, 400), cos, eps, rng.uniform(0, 2 * math.pi, 400)):
+        u1, ue, E1, T = oracle.compton_kinematics(E, u, c, e, phi)
+        assert E1 + T == pytest.approx(E, rel=1e-14)
+        assert float(u @ u1) == pytest.approx(c, abs=1e-12)
+        pe = math.sqrt(T * (T + 2.0 * MC2))
+        np.testing.assert_allclose(E * u, E1 * u1 + pe * ue, atol=1e-10 * E)
+
+
+@pytest.mark.parametrize("T", [0.45, 2.0, 15.0])
+def test_moller_kinematics_conserve_momentum(T):
+    """GPUMCD §II.B.1 Moller: the knock-on and the scattered electron at
+    azimuths phi and phi + pi conserve the incident momentum along and across
+    the incident direction, p_k cos_k + p_s cos_s = p and p_k sin_k = p_s sin_s."""
+    eps = oracle.sample("moller", 300, 23, T, P.t_c)
+    p = math.sqrt(T * (T + 2.0 * MC2))
+    for e in eps:
+        tk, ts, ck, cs = oracle.moller_kinematics(T, e)
+        assert tk + ts == pytest.approx(T, rel=1e-14)
+        assert tk == pytest.approx(e * T, rel=1e-14)
+        pk, ps = math.sqrt(tk * (tk + 2.0 * MC2)), math.sqrt(ts * (ts + 2.0 * MC2))
+        assert pk * ck + ps * cs == pytest.approx(p, rel=1e-10)
+        assert pk * math.sqrt(max(0.0, 1.0 - ck * ck)) == pytest.approx(
+            ps * math.sqrt(max(0.0, 1.0 - cs * cs)), rel=1e-8, abs=1e-12)
+
+
+def test_electron_woodcock_invariance_far_dense_voxel():
+    """GPUMCD §II.B.3, the electron Woodcock test: one far-away dense voxel
+    raises the electron majorant; fictitious hard events multiply, but the rate
+    of real hard events and the dose elsewhere do not change."""
+    base = W.homogeneous((16, 16, 24), 0.5, W.MAT_WATER, 1.0)
+    dense = W.homogeneous((16, 16, 24), 0.5, W.MAT_WATER, 1.0)
+    dense.mat[23, 15, 15] = W.MAT_BONE
+    dense.rho[23, 15, 15] = 2.0
+    src = W.square_field(W.ELECTRON, 6.0, base, 4.0)
+    n, parts = 16000, 8
+    procs = min(host_cores(), parts)
+    a = oracle.simulate_parts(W.MATERIALS, P, base, src, n, 11, parts, processes=procs)
+    b = oracle.simulate_parts(W.MATERIALS, P, dense, src, n, 12, parts, processes=procs)
+    fa = sum(r.stats["n_hard_fict"] for r in a)
+    fb = sum(r.stats["n_hard_fict"] for r in b)
+    assert fb > 3 * max(fa, 1)  # the majorant really was raised
+    ra = np.array([r.stats["n_hard_real"] for r in a], dtype=float)
+    rb = np.array([r.stats["n_hard_real"] for r in b], dtype=float)
+    se = math.sqrt(ra.var(ddof=1) / parts + rb.var(ddof=1) / parts)
+    assert abs(ra.mean() - rb.mean()) <= 4.0 * se, (ra.mean(), rb.mean(), se)
+
+    def merged(rs, ph):
+        tot = oracle.OracleResult(n, sum(r.sum_e for r in rs), sum(r.sum_e2 for r in rs), {})
+        return tot.dose_gy(ph), tot.sigma_gy(ph)
+
+    da, sa = merged(a, base)
+    db, sb = merged(b, dense)
+    mask = da > 0.1 * da.max()
+    mask[23 * 16 * 16 + 15 * 16 + 15] = False
+    assert mask.sum() > 50
+    assert three_sigma_pass_rate(da, sa, db, sb, mask) >= 0.98
+
+
+def test_history_by_history_sigma_matches_the_spread_of_independent_runs():
+    """GPUMCD §II.D: the Delta D estimator of one run of n histories predicts
+    the scatter of the dose over independent runs of n.  24 disjoint history
+    ranges: the mean over high-dose voxels of (sample variance of the 24
+    doses) / (mean estimated sigma^2) is 1 within its sampling error."""
+    ph = W.homogeneous((12, 12, 20), 0.5, W.MAT_WATER, 1.0)
+    src = W.pencil(W.PHOTON, 2.0, 3.0, 3.0)
+    parts, n_part = 24, 2000
+    rs = oracle.simulate_parts(W.MATERIALS, P, ph, src, parts * n_part, 31, parts,
+                               processes=min(host_cores(), parts))
+    d = np.array([r.dose_gy(ph) for r in rs])
+    s2 = np.array([r.sigma_gy(ph) ** 2 for r in rs])
+    dm = d.mean(axis=0)
+    mask = dm > 0.2 * dm.max()
+    assert mask.sum() >= 20
+    ratio = d[:, mask].var(axis=0, ddof=1) / s2[:, mask].mean(axis=0)
+    # each ratio has relative spread ~ sqrt(2/23) = 0.29 (plus skew); their mean is 1
+    assert float(ratio.mean()) == pytest.approx(1.0, abs=3.0 * 0.35 / math.sqrt(mask.sum()) + 0.05)
+    # sigma itself scales as 1/sqrt(n): the merged run's sigma is 1/sqrt(24) of a part's
+    tot = oracle.OracleResult(parts * n_part, sum(r.sum_e for r in rs), sum(r.sum_e2 for r in rs), {})
+    st = tot.sigma_gy(ph)[mask]
+    sp = np.sqrt(s2[:, mask].mean(axis=0))
+    assert float(np.median(st * math.sqrt(parts) / sp)) == pytest.approx(1.0, abs=0.05)

@@ -3,7 +3,8 @@
 The oracle only needs a good generator to be a correct Monte Carlo; these CPU
 checks cover uniformity, bit balance, counter and key sensitivity.  Its exact
 identity with the published Philox4x32-10 is pinned on the GPU against cuRAND's
-Philox4_32_10 device generator (tests/test_gpu_rng.py).
+Philox4_32_10 device generator
+(tests/test_gpu_physics.py::test_philox_matches_curand_and_oracle).
 """
 import numpy as np
 from scipy import stats
