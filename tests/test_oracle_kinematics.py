@@ -194,3 +194,33 @@ def test_history_by_history_sigma_matches_the_spread_of_independent_runs():
     st = tot.sigma_gy(ph)[mask]
     sp = np.sqrt(s2[:, mask].mean(axis=0))
     assert float(np.median(st * math.sqrt(parts) / sp)) == pytest.approx(1.0, abs=0.05)
+
+
+def test_real_hard_event_rate_in_a_thin_slab_equals_the_cross_section():
+    """GPUMCD §II.B.3: however the majorant is set, real hard events occur at
+    the rate rho Sigma_hard(T) per unit path.  An electron pencil runs straight
+    (no multiple scattering) through 0.5 cm of water with the Moller threshold
+    out of reach (t_c = 9.9 MeV) and every photon absorbed where it is made
+    (p_cut = 15 MeV), so the only hard events are the primary's bremsstrahlung.
+    Their count per history equals rho times the integral of Sigma_brem(T(x))
+    along the CSDA energy T(x), within its statistics (and ~0.3% for the energy
+    a hard event itself removes)."""
+    import dataclasses
+    from scipy import integrate
+
+    phys = dataclasses.replace(P, t_c=9.9, p_cut=15.0)
+    ph = W.homogeneous((40, 40, 1), 0.5, W.MAT_WATER, 1.0)
+    T0, n = 10.0, 200_000
+    src = W.pencil(W.ELECTRON, T0, 10.0, 10.0)
+    r = oracle.simulate(W.MATERIALS, phys, ph, src, n, 41, oracle.FLAG_NO_MS, processes=host_cores())
+    assert r.stats["n_moller"] == 0 and r.stats["n_hard_real"] == r.stats["n_brem"]
+
+    def loss(x, T):  # restricted CSDA loss per cm in water
+        return [-(oracle.xs("l_col", W.WATER, T[0], phys.t_c) + oracle.xs("l_rad", W.WATER, T[0], phys.k_c))]
+
+    sol = integrate.solve_ivp(loss, (0.0, 0.5), [T0], rtol=1e-10, atol=1e-12, dense_output=True)
+    expect, _ = integrate.quad(lambda x: oracle.xs("sigma_brem", W.WATER, float(sol.sol(x)[0]), phys.k_c),
+                               0.0, 0.5, epsabs=1e-12)
+    got = r.stats["n_hard_real"] / n
+    se = math.sqrt(got / n)
+    assert abs(got - expect) <= 3.0 * se + 0.003 * expect, (got, expect, se)
