@@ -2,6 +2,8 @@
 // packing, majorants, spectrum CDF, the dose/uncertainty fold and reductions.
 #include <curand_kernel.h>
 
+#include <mutex>
+
 #include "gm_common.cuh"
 #include "gm_host.h"
 
@@ -322,6 +324,34 @@ struct FoldArgs {
     double n_b[64];
 };
 
+// Per-voxel arithmetic of the fold with per-batch history counts n_b: the
+// mean energy per history and the batch-mean variance, scaled to Gy.
+template <int W>
+__device__ __forceinline__ void fold_voxel(const unsigned long long *tally, const uint32_t *vox, uint64_t nvox,
+                                           uint64_t v, const FoldArgs &fa, double n_tot, double inv_vol,
+                                           double &dv, double &sv, unsigned long long &tot_out) {
+    unsigned long long s[W];
+    unsigned long long tot = 0;
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+        s[b] = __ldcs(tally + (uint64_t)b * nvox + v);
+        tot += s[b];
+    }
+    const double mean = (double)tot / n_tot;
+    double acc = 0.0;
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+        const double t = fma(-fa.n_b[b], mean, (double)s[b]);
+        acc = fma(t, t, acc);
+    }
+    const double var = acc * ((double)W / ((double)(W - 1) * n_tot * n_tot));
+    const double rho = (double)(vox[v] >> 4) * (double)kRhoQ;
+    const double scale = kQ * kMeVPerGramToGy * inv_vol / rho;
+    dv = mean * scale;
+    sv = sqrt(var) * scale;
+    tot_out = tot;
+}
+
 template <int W>
 __global__ void k_fold(const unsigned long long *tally, const uint32_t *vox, uint64_t nvox,
                        const __grid_constant__ FoldArgs fa, double n_tot, double inv_vol, double *dose,
@@ -330,26 +360,11 @@ __global__ void k_fold(const unsigned long long *tally, const uint32_t *vox, uin
     unsigned long long local_sum = 0;
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < nvox;
          v += (uint64_t)gridDim.x * blockDim.x) {
-        unsigned long long s[W];
-        unsigned long long tot = 0;
-#pragma unroll
-        for (int b = 0; b < W; ++b) {
-            s[b] = __ldcs(tally + (uint64_t)b * nvox + v);
-            tot += s[b];
-        }
-        const double mean = (double)tot / n_tot;
-        double acc = 0.0;
-#pragma unroll
-        for (int b = 0; b < W; ++b) {
-            const double t = fma(-fa.n_b[b], mean, (double)s[b]);
-            acc = fma(t, t, acc);
-        }
-        const double var = acc * ((double)W / ((double)(W - 1) * n_tot * n_tot));
-        const double rho = (double)(vox[v] >> 4) * (double)kRhoQ;
-        const double scale = kQ * kMeVPerGramToGy * inv_vol / rho;
-        const double dv = mean * scale;
+        double dv, sv;
+        unsigned long long tot;
+        fold_voxel<W>(tally, vox, nvox, v, fa, n_tot, inv_vol, dv, sv, tot);
         if (dose) dose[v] = dv;
-        if (sigma) sigma[v] = sqrt(var) * scale;
+        if (sigma) sigma[v] = sv;
         local_max = fmax(local_max, dv);
         local_sum += tot;
     }
@@ -394,6 +409,43 @@ struct FoldConst {
     double k_dose;  // q * (MeV/g -> Gy) / (voxel volume * density quantum)
 };
 
+// Per-voxel arithmetic of the equal-batch fold.
+template <int W>
+__device__ __forceinline__ void fold_voxel_equal(const unsigned long long *tally, const uint32_t *vox,
+                                                 uint64_t nvox, uint64_t v, const FoldConst &fc, double &dv,
+                                                 double &sv, unsigned long long &tot_out) {
+    unsigned long long s[W];
+    unsigned long long tot = 0;
+    U128 sq{0ull, 0ull};
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+        s[b] = __ldcs(tally + (uint64_t)b * nvox + v);
+        tot += s[b];
+        add_sq(sq, s[b]);
+    }
+    double var_sum;  // sum_b (S_b - S/W)^2, in quanta^2
+    if (sq.hi < (1ull << 57)) {
+        // W sum S_b^2 - S^2, exact and non-negative (Cauchy-Schwarz), = W var_sum
+        const U128 ws{sq.lo * (unsigned long long)W, sq.hi * (unsigned long long)W + __umul64hi(sq.lo, (unsigned long long)W)};
+        const U128 t2{tot * tot, __umul64hi(tot, tot)};
+        const U128 num{ws.lo - t2.lo, ws.hi - t2.hi - (ws.lo < t2.lo ? 1ull : 0ull)};
+        var_sum = u128_to_double(num) * (1.0 / (double)W);
+    } else {
+        const double m = (double)tot * (1.0 / (double)W);
+        double acc = 0.0;
+        for (int b = 0; b < W; ++b) {
+            const double t = (double)s[b] - m;
+            acc = fma(t, t, acc);
+        }
+        var_sum = acc;
+    }
+    // var(D) = var_sum / (W (W - 1) n^2) in quanta^2 per history^2
+    const double r = fc.k_dose / (double)(vox[v] >> 4);
+    dv = (double)tot * fc.inv_n * r;
+    sv = sqrt(var_sum * ((double)W * fc.c_var)) * r;
+    tot_out = tot;
+}
+
 template <int W>
 __global__ void k_fold_equal(const unsigned long long *tally, const uint32_t *vox, uint64_t nvox, FoldConst fc,
                              double *dose, double *sigma, unsigned long long *dmax_bits,
@@ -402,36 +454,11 @@ __global__ void k_fold_equal(const unsigned long long *tally, const uint32_t *vo
     unsigned long long local_sum = 0;
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < nvox;
          v += (uint64_t)gridDim.x * blockDim.x) {
-        unsigned long long s[W];
-        unsigned long long tot = 0;
-        U128 sq{0ull, 0ull};
-#pragma unroll
-        for (int b = 0; b < W; ++b) {
-            s[b] = __ldcs(tally + (uint64_t)b * nvox + v);
-            tot += s[b];
-            add_sq(sq, s[b]);
-        }
-        double var_sum;  // sum_b (S_b - S/W)^2, in quanta^2
-        if (sq.hi < (1ull << 57)) {
-            // W sum S_b^2 - S^2, exact and non-negative (Cauchy-Schwarz), = W var_sum
-            const U128 ws{sq.lo * (unsigned long long)W, sq.hi * (unsigned long long)W + __umul64hi(sq.lo, (unsigned long long)W)};
-            const U128 t2{tot * tot, __umul64hi(tot, tot)};
-            const U128 num{ws.lo - t2.lo, ws.hi - t2.hi - (ws.lo < t2.lo ? 1ull : 0ull)};
-            var_sum = u128_to_double(num) * (1.0 / (double)W);
-        } else {
-            const double m = (double)tot * (1.0 / (double)W);
-            double acc = 0.0;
-            for (int b = 0; b < W; ++b) {
-                const double t = (double)s[b] - m;
-                acc = fma(t, t, acc);
-            }
-            var_sum = acc;
-        }
-        // var(D) = var_sum / (W (W - 1) n^2) in quanta^2 per history^2
-        const double r = fc.k_dose / (double)(vox[v] >> 4);
-        const double dv = (double)tot * fc.inv_n * r;
+        double dv, sv;
+        unsigned long long tot;
+        fold_voxel_equal<W>(tally, vox, nvox, v, fc, dv, sv, tot);
         if (dose) dose[v] = dv;
-        if (sigma) sigma[v] = sqrt(var_sum * ((double)W * fc.c_var)) * r;
+        if (sigma) sigma[v] = sv;
         local_max = fmax(local_max, dv);
         local_sum += tot;
     }
@@ -446,9 +473,16 @@ __global__ void k_fold_equal(const unsigned long long *tally, const uint32_t *vo
 }
 
 // s_thr = mean of sigma/D over voxels with D > thr * D_max (GPUMCD §II.D, s).
-__global__ void k_sthr(const double *dose, const double *sigma, uint64_t nvox,
-                       const unsigned long long *dmax_bits, double thr, double *sum,
-                       unsigned long long *count) {
+// Each block writes its partial sum and count to its own slot; one block then
+// adds the slots in a fixed order, so s_thr is the same bit for bit for the
+// same tally (the run-to-uncertainty schedule depends on it).
+constexpr int kSthrThreads = 256;
+
+__global__ void __launch_bounds__(kSthrThreads) k_sthr(const double *dose, const double *sigma, uint64_t nvox,
+                                                       const unsigned long long *dmax_bits, double thr,
+                                                       double2 *part) {
+    __shared__ double ss[kSthrThreads / 32];
+    __shared__ double sc[kSthrThreads / 32];
     const double cut = thr * __longlong_as_double((long long)*dmax_bits);
     double s = 0.0;
     unsigned long long c = 0;
@@ -464,9 +498,43 @@ __global__ void k_sthr(const double *dose, const double *sigma, uint64_t nvox,
         s += __shfl_xor_sync(0xffffffffu, s, o);
         c += __shfl_xor_sync(0xffffffffu, c, o);
     }
-    if ((threadIdx.x & 31) == 0 && c) {
-        atomicAdd(sum, s);
-        atomicAdd(count, c);
+    if ((threadIdx.x & 31) == 0) {
+        ss[threadIdx.x >> 5] = s;
+        sc[threadIdx.x >> 5] = (double)c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < kSthrThreads / 32; ++i) {
+            a += ss[i];
+            b += sc[i];
+        }
+        part[blockIdx.x] = make_double2(a, b);
+    }
+}
+
+__global__ void __launch_bounds__(kSthrThreads) k_sthr_combine(const double2 *part, int n, double *sum,
+                                                               unsigned long long *count) {
+    __shared__ double ss[kSthrThreads];
+    __shared__ double sc[kSthrThreads];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < n; i += kSthrThreads) {
+        a += part[i].x;
+        b += part[i].y;
+    }
+    ss[threadIdx.x] = a;
+    sc[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = kSthrThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            ss[threadIdx.x] += ss[threadIdx.x + w];
+            sc[threadIdx.x] += sc[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *sum = ss[0];
+        *count = (unsigned long long)sc[0];
     }
 }
 
@@ -553,24 +621,36 @@ cudaError_t launch_spectrum(const double *edges, const double *w, int n, float *
     return cudaGetLastError();
 }
 
-cudaError_t launch_fold(const unsigned long long *tally, const uint32_t *vox, uint64_t nvox, int W,
-                        const double *n_b, double n_tot, double inv_vol, double *dose, double *sigma,
-                        unsigned long long *dmax_bits, unsigned long long *dep_sum, int n_sm, cudaStream_t s) {
-    FoldArgs fa;
+// Host side of both folds: the per-batch history counts and whether they are
+// all equal (the integer-variance form), and the constants of that form.
+static bool fold_args(int W, const double *n_b, FoldArgs &fa) {
     bool equal = true;
     for (int b = 0; b < 64; ++b) {
         fa.n_b[b] = b < W ? n_b[b] : 0.0;
         if (b < W && n_b[b] != n_b[0]) equal = false;
     }
+    return equal;
+}
+
+static FoldConst fold_const(int W, double n_tot, double inv_vol) {
+    FoldConst fc;
+    const double n = n_tot / (double)W;
+    fc.inv_n = 1.0 / n_tot;
+    fc.c_var = 1.0 / ((double)W * (double)W * (double)(W - 1) * n * n);
+    fc.k_dose = kQ * kMeVPerGramToGy * inv_vol / kRhoQ;
+    return fc;
+}
+
+cudaError_t launch_fold(const unsigned long long *tally, const uint32_t *vox, uint64_t nvox, int W,
+                        const double *n_b, double n_tot, double inv_vol, double *dose, double *sigma,
+                        unsigned long long *dmax_bits, unsigned long long *dep_sum, int n_sm, cudaStream_t s) {
+    FoldArgs fa;
+    const bool equal = fold_args(W, n_b, fa);
     uint64_t blocks = (nvox + 255) / 256;
     const uint64_t cap = (uint64_t)n_sm * 8;
     const int grid = (int)(blocks < cap ? (blocks ? blocks : 1) : cap);
     if (equal) {
-        FoldConst fc;
-        const double n = n_tot / (double)W;
-        fc.inv_n = 1.0 / n_tot;
-        fc.c_var = 1.0 / ((double)W * (double)W * (double)(W - 1) * n * n);
-        fc.k_dose = kQ * kMeVPerGramToGy * inv_vol / kRhoQ;
+        const FoldConst fc = fold_const(W, n_tot, inv_vol);
         switch (W) {
             case 8: k_fold_equal<8><<<grid, 256, 0, s>>>(tally, vox, nvox, fc, dose, sigma, dmax_bits, dep_sum); break;
             case 16: k_fold_equal<16><<<grid, 256, 0, s>>>(tally, vox, nvox, fc, dose, sigma, dmax_bits, dep_sum); break;
@@ -590,13 +670,18 @@ cudaError_t launch_fold(const unsigned long long *tally, const uint32_t *vox, ui
     return cudaGetLastError();
 }
 
+int sthr_blocks(uint64_t nvox, int n_sm) {
+    const uint64_t blocks = (nvox + kSthrThreads - 1) / kSthrThreads;
+    const uint64_t cap = (uint64_t)n_sm * 8;
+    return (int)(blocks < cap ? (blocks ? blocks : 1) : cap);
+}
+
 cudaError_t launch_sthr(const double *dose, const double *sigma, uint64_t nvox,
                         const unsigned long long *dmax_bits, double thr, double *sum,
-                        unsigned long long *count, int n_sm, cudaStream_t s) {
-    uint64_t blocks = (nvox + 255) / 256;
-    const uint64_t cap = (uint64_t)n_sm * 8;
-    k_sthr<<<(int)(blocks < cap ? (blocks ? blocks : 1) : cap), 256, 0, s>>>(dose, sigma, nvox, dmax_bits,
-                                                                          thr, sum, count);
+                        unsigned long long *count, void *part, int n_sm, cudaStream_t s) {
+    const int grid = sthr_blocks(nvox, n_sm);
+    k_sthr<<<grid, kSthrThreads, 0, s>>>(dose, sigma, nvox, dmax_bits, thr, (double2 *)part);
+    k_sthr_combine<<<1, kSthrThreads, 0, s>>>((const double2 *)part, grid, sum, count);
     return cudaGetLastError();
 }
 
@@ -622,7 +707,8 @@ cudaError_t launch_philox(const uint32_t *ctr, uint2 key, uint64_t n, int curand
 // ---------------------------------------------------------------------------
 // Allocation-free fold (gpumcd_plan_result_noalloc).
 //
-// The same dose / uncertainty fold as k_fold, with its reduction scratch in a
+// The same dose / uncertainty fold as k_fold and k_fold_equal (the same
+// per-voxel functions), with its reduction scratch in a
 // file-scope device array instead of device memory allocated at run time.
 // Each block folds one fixed range of voxels and writes its partial results
 // to its own slots of the array; single-block kernels then combine the
@@ -642,10 +728,14 @@ static_assert((uint64_t)kMaxBlocks * kVoxPerBlock == GPUMCD_NOALLOC_MAX_VOXELS, 
 // count) followed by 4 result words (D_max bits, deposited, s_thr bits, count).
 static __device__ __align__(256) unsigned long long scratch[kMaxBlocks * 4 + 4];
 
-template <int W>
-__global__ void k_fold_blocks(const unsigned long long *tally, const uint32_t *vox, uint64_t nvox,
-                              const __grid_constant__ FoldArgs fa, double n_tot, double inv_vol,
-                              double *dose, double *sigma, unsigned long long *part) {
+// EQUAL selects the integer-variance form of k_fold_equal, else the form of
+// k_fold: the per-voxel arithmetic is the same function as the regular
+// fold's, so dose and sigma match gpumcd_plan_result's bit for bit.
+template <int W, bool EQUAL>
+__global__ void __launch_bounds__(kThreads) k_fold_blocks(const unsigned long long *tally, const uint32_t *vox,
+                                                          uint64_t nvox, const __grid_constant__ FoldArgs fa,
+                                                          FoldConst fc, double n_tot, double inv_vol, double *dose,
+                                                          double *sigma, unsigned long long *part) {
     __shared__ double smax[kThreads / 32];
     __shared__ unsigned long long ssum[kThreads / 32];
     const uint64_t v0 = blockIdx.x * kVoxPerBlock;
@@ -654,26 +744,14 @@ __global__ void k_fold_blocks(const unsigned long long *tally, const uint32_t *v
     for (int k = 0; k < kVoxPerThread; ++k) {
         const uint64_t v = v0 + (uint64_t)k * kThreads + threadIdx.x;
         if (v >= nvox) break;
-        unsigned long long s[W];
-        unsigned long long tot = 0;
-#pragma unroll
-        for (int b = 0; b < W; ++b) {
-            s[b] = __ldcs(tally + (uint64_t)b * nvox + v);
-            tot += s[b];
-        }
-        const double mean = (double)tot / n_tot;
-        double acc = 0.0;
-#pragma unroll
-        for (int b = 0; b < W; ++b) {
-            const double t = fma(-fa.n_b[b], mean, (double)s[b]);
-            acc = fma(t, t, acc);
-        }
-        const double var = acc * ((double)W / ((double)(W - 1) * n_tot * n_tot));
-        const double rho = (double)(vox[v] >> 4) * (double)kRhoQ;
-        const double scale = kQ * kMeVPerGramToGy * inv_vol / rho;
-        const double dv = mean * scale;
+        double dv, sv;
+        unsigned long long tot;
+        if (EQUAL)
+            fold_voxel_equal<W>(tally, vox, nvox, v, fc, dv, sv, tot);
+        else
+            fold_voxel<W>(tally, vox, nvox, v, fa, n_tot, inv_vol, dv, sv, tot);
         dose[v] = dv;
-        sigma[v] = sqrt(var) * scale;
+        sigma[v] = sv;
         local_max = fmax(local_max, dv);
         local_sum += tot;
     }
@@ -793,43 +871,60 @@ __global__ void k_combine_sthr(unsigned long long *part, int n_blocks) {
 
 // The address of the scratch array on `device`, looked up once per device
 // with that device current.  In host code the array's name is only a host-side
-// stand-in, so kernels must be given this address instead.
+// stand-in, so kernels must be given this address instead.  Host threads may
+// make their first calls at the same time, so the lookup is done under a lock.
 static unsigned long long *noalloc_scratch(int device, cudaError_t *err) {
+    static std::mutex mu;
     static unsigned long long *addr[64] = {nullptr};
-    static bool done[64] = {false};
     if (device < 0 || device >= 64) {
         *err = cudaErrorInvalidDevice;
         return nullptr;
     }
-    if (!done[device]) {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[device]) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, noalloc::scratch);
         if (e != cudaSuccess) {
             *err = e;
             return nullptr;
         }
+        if (!p) {
+            *err = cudaErrorInvalidDevicePointer;
+            return nullptr;
+        }
         addr[device] = (unsigned long long *)p;
-        done[device] = true;
     }
     *err = cudaSuccess;
     return addr[device];
 }
 
+template <int W>
+static void launch_fold_blocks(bool equal, int nb, cudaStream_t s, const unsigned long long *tally,
+                               const uint32_t *vox, uint64_t nvox, const FoldArgs &fa, const FoldConst &fc,
+                               double n_tot, double inv_vol, double *dose, double *sigma, unsigned long long *part) {
+    using namespace noalloc;
+    if (equal)
+        k_fold_blocks<W, true><<<nb, kThreads, 0, s>>>(tally, vox, nvox, fa, fc, n_tot, inv_vol, dose, sigma, part);
+    else
+        k_fold_blocks<W, false><<<nb, kThreads, 0, s>>>(tally, vox, nvox, fa, fc, n_tot, inv_vol, dose, sigma, part);
+}
+
 cudaError_t launch_fold_noalloc(int device, const unsigned long long *tally, const uint32_t *vox, uint64_t nvox,
                                 int W, const double *n_b, double n_tot, double inv_vol, double thr, double *dose,
                                 double *sigma, cudaStream_t s, unsigned long long result[4]) {
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
     unsigned long long *part = noalloc_scratch(device, &e);
-    if (!part) return e;
+    if (!part) return e != cudaSuccess ? e : cudaErrorInvalidDevicePointer;
     FoldArgs fa;
-    for (int b = 0; b < 64; ++b) fa.n_b[b] = b < W ? n_b[b] : 0.0;
+    const bool equal = fold_args(W, n_b, fa);
+    const FoldConst fc = fold_const(W, n_tot, inv_vol);
     const int nb = (int)((nvox + noalloc::kVoxPerBlock - 1) / noalloc::kVoxPerBlock);
     using namespace noalloc;
     switch (W) {
-        case 8: k_fold_blocks<8><<<nb, kThreads, 0, s>>>(tally, vox, nvox, fa, n_tot, inv_vol, dose, sigma, part); break;
-        case 16: k_fold_blocks<16><<<nb, kThreads, 0, s>>>(tally, vox, nvox, fa, n_tot, inv_vol, dose, sigma, part); break;
-        case 32: k_fold_blocks<32><<<nb, kThreads, 0, s>>>(tally, vox, nvox, fa, n_tot, inv_vol, dose, sigma, part); break;
-        case 64: k_fold_blocks<64><<<nb, kThreads, 0, s>>>(tally, vox, nvox, fa, n_tot, inv_vol, dose, sigma, part); break;
+        case 8: launch_fold_blocks<8>(equal, nb, s, tally, vox, nvox, fa, fc, n_tot, inv_vol, dose, sigma, part); break;
+        case 16: launch_fold_blocks<16>(equal, nb, s, tally, vox, nvox, fa, fc, n_tot, inv_vol, dose, sigma, part); break;
+        case 32: launch_fold_blocks<32>(equal, nb, s, tally, vox, nvox, fa, fc, n_tot, inv_vol, dose, sigma, part); break;
+        case 64: launch_fold_blocks<64>(equal, nb, s, tally, vox, nvox, fa, fc, n_tot, inv_vol, dose, sigma, part); break;
         default: return cudaErrorInvalidValue;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -26,15 +26,21 @@ def _noalloc(ctx, plan, dose, sigma):
     return status, st.as_dict()
 
 
-def test_noalloc_result_matches_plan_result_twice():
+@pytest.mark.parametrize("n_batches", [8, 16, 32, 64])
+def test_noalloc_result_matches_plan_result_twice(n_batches):
+    """Two calls in a row on one plan, each against gpumcd_plan_result: the
+    first after 30,005 histories (unequal batches: the two-pass FP64 form),
+    the second after 40,000 (equal batches: the integer-variance form).  Both
+    calls use the regular fold's per-voxel arithmetic, so dose and sigma are
+    equal bit for bit; s_thr sums in another order (relative 1e-12)."""
     import torch
     ctx = make_ctx()
     ph = W.z_slabs((40, 36, 48), 0.5, [(3.0, W.MAT_WATER, 1.0), (2.0, W.MAT_BONE, 1.85),
                                         (5.0, W.MAT_LUNG, 0.26), (1e9, W.MAT_WATER, 1.0)])
     pid = ctx.create_phantom(ph)
     src = W.Source(W.ELECTRON, W.BEAM_SQUARE, energy=9.0, center_cm=(10.0, 9.0), field_cm=6.0)
-    plan = ctx.plan_open(pid, src, 21, 32)
-    ctx.run([plan], [30_000])
+    plan = ctx.plan_open(pid, src, 21, n_batches)
+    ctx.run([plan], [30_005])
     d_ref = torch.zeros(ph.nvox, dtype=torch.float64, device="cuda")
     s_ref = torch.zeros_like(d_ref)
     ref = ctx.plan_result(plan, 0.5, d_ref.data_ptr(), s_ref.data_ptr())
@@ -45,16 +51,17 @@ def test_noalloc_result_matches_plan_result_twice():
         status, st = _noalloc(ctx, plan, d, s)
         assert status == g.OK, g.status_string(status)
         assert ctx.memory()[0] == used_before  # nothing allocated through the context
-        assert torch.allclose(d, d_ref, rtol=1e-12, atol=0.0)
-        assert torch.allclose(s, s_ref, rtol=1e-12, atol=0.0)
-        assert st["d_max_gy"] == pytest.approx(ref["d_max_gy"], rel=1e-12)
+        assert torch.equal(d, d_ref)
+        assert torch.equal(s, s_ref)
+        assert st["d_max_gy"] == ref["d_max_gy"]
         assert st["s_thr"] == pytest.approx(ref["s_thr"], rel=1e-12)
-        for k in ("e_deposited", "e_incident", "e_escaped", "e_rest", "histories"):
+        for k in ("e_deposited", "e_incident", "e_escaped", "e_rest", "histories", "n_batches"):
             assert st[k] == ref[k], k
         if call == 0:
             # more histories between the two calls: the array keeps nothing stale
-            ctx.run([plan], [10_000])
+            ctx.run([plan], [9_995])
             ref = ctx.plan_result(plan, 0.5, d_ref.data_ptr(), s_ref.data_ptr())
+            assert ref["histories"] % n_batches == 0
             used_before = ctx.memory()[0]
     ctx.plan_close(plan)
     ctx.destroy_phantom(pid)
