@@ -63,16 +63,20 @@ typedef int32_t gpumcd_status;
  * - a phase space's records are stably sorted by decreasing E at
  *   gpumcd_plan_open; history h takes record h mod n of the sorted list (ties
  *   keep their listed order);
- * - a spectrum is sampled stratified within each run: of the n histories one
- *   gpumcd_run (or gpumcd_simulate pass) gives the plan, the j-th draws the
- *   cumulative-spectrum quantile 1 - (j + u)/n, u its own uniform draw.  Each
- *   run is then one draw from each of n equal-probability strata, highest
- *   energies first; the tally depends on how the histories are split into
- *   runs (the same sizes reproduce it bit for bit);
+ * - a spectrum is sampled stratified over aligned blocks of 2^16 histories:
+ *   history h, j = h mod 2^16 in block k = h / 2^16, draws the cumulative-
+ *   spectrum quantile (s + u)/2^16 with u its own uniform draw and stratum
+ *   s = (64 bitrev10(j / 64) + j mod 64 + r_k) mod 2^16, r_k a uniform draw
+ *   of the block keyed by the plan's seed.  64 consecutive histories take
+ *   consecutive strata (similar energies), the chunks of 64 follow the
+ *   bit-reversed order (a part of a block spreads over the whole spectrum),
+ *   and a whole block takes every stratum once.  Over r_k each history's
+ *   quantile is uniform, so any history count is unbiased; the energy
+ *   depends on the history index alone, so the tally does not depend on how
+ *   the histories are split into runs, batched or served;
  * - a monoenergetic beam is unchanged.
- * Either way the long high-energy histories are claimed first and the short
- * ones last.  A launch holding a grouped spectral plan runs the phase-space
- * kernel, with its restrictions. */
+ * A launch holding a grouped spectral plan runs the phase-space kernel, with
+ * its restrictions. */
 #define GPUMCD_ENERGY_UNGROUPED 0
 #define GPUMCD_ENERGY_GROUPED 1
 
@@ -300,6 +304,39 @@ gpumcd_status gpumcd_plan_result(gpumcd_ctx *ctx, int32_t plan_id, double thresh
                                  double *dose_out, double *sigma_out, void *stream,
                                  gpumcd_run_stats *stats);
 
+/* gpumcd_plan_result with host outputs: dose_out and sigma_out are host arrays
+ * of nx*ny*nz doubles (either may be NULL; pinned memory copies fastest).  The
+ * fold runs on the context's stream into the context's scratch and both arrays
+ * are copied back before the call returns.  Errors as gpumcd_plan_result. */
+gpumcd_status gpumcd_plan_result_host(gpumcd_ctx *ctx, int32_t plan_id, double threshold_frac,
+                                      double *dose_out, double *sigma_out, gpumcd_run_stats *stats);
+
+/* Runs plans to a target uncertainty (§II.D: s, the mean of sigma/D over the
+ * voxels with dose above threshold_frac x D_max; the "1% uncertainty" of a
+ * dose calculation).  All n_plans <= GPUMCD_MAX_PLANS_PER_RUN distinct plans
+ * (host array plan_ids) run together in rounds, each round one gpumcd_run on
+ * `stream` over the plans still above the target, followed by their folds.
+ * In the first round plan i runs first_histories[i] more histories; after
+ * each round a plan with N histories and uncertainty s > target is given
+ * enough to reach max(1.05 N (s/target)^2, 1.1 N), since s falls as 1/sqrt(N).
+ * Every round's count is a whole multiple of the plan's n_batches (equal
+ * batches) and a plan stops at max_histories[i] in total.  A plan's schedule
+ * depends on its own results only, so running plans together or one by one
+ * gives the same histories and, bit for bit, the same tallies.  Outputs (host,
+ * optional): histories_out[i] the plan's total histories, s_thr_out[i] its
+ * final s (infinity if no dose), *rounds_out the rounds run and
+ * *transport_ms_out the device time of their transport launches.  Plans continue
+ * from the histories they hold.  Errors: GPUMCD_ERR_INVALID_ARG (target <= 0,
+ * threshold outside [0, 1], first_histories[i] = 0, max_histories[i] below
+ * first_histories[i] or above 2^32, a repeated id), GPUMCD_ERR_NOT_FOUND,
+ * GPUMCD_ERR_STATE (a plan in flight or failed), or any error of gpumcd_run
+ * or gpumcd_plan_result (the plans then hold the rounds that finished). */
+gpumcd_status gpumcd_run_to_uncertainty(gpumcd_ctx *ctx, int32_t n_plans, const int32_t *plan_ids,
+                                        const uint64_t *first_histories, const uint64_t *max_histories,
+                                        double target_rel_unc, double threshold_frac, void *stream,
+                                        uint64_t *histories_out, double *s_thr_out, uint32_t *rounds_out,
+                                        double *transport_ms_out);
+
 /* Histories of a plan's finished sequences. */
 gpumcd_status gpumcd_plan_histories(gpumcd_ctx *ctx, int32_t plan_id, uint64_t *histories);
 
@@ -313,7 +350,9 @@ gpumcd_status gpumcd_memory(gpumcd_ctx *ctx, uint64_t *used_bytes, uint64_t *bud
 
 /* The paper has no counterpart to this call.
  *
- * Same result as gpumcd_plan_result, but the call allocates no memory at all.
+ * The same dose and sigma as gpumcd_plan_result, bit for bit (it uses the same
+ * per-voxel arithmetic), and the same stats (s_thr to about 1e-12 relative, as
+ * it sums in another order), but the call allocates no memory at all.
  * It is meant for callers that cannot allocate device memory when they ask for
  * a result: a serving loop whose HBM budget is already committed in full to
  * resident phantoms and tallies, or a latency-bound loop in which a
@@ -324,10 +363,12 @@ gpumcd_status gpumcd_memory(gpumcd_ctx *ctx, uint64_t *used_bytes, uint64_t *bud
  * code, which every GPU that loads the library holds until the process exits.
  * That array bounds the phantom to GPUMCD_NOALLOC_MAX_VOXELS voxels; a larger
  * phantom returns GPUMCD_ERR_INVALID_ARG.  The first call on a device looks up
- * the array's device address, so make that first call before any stream
- * capture.  Every call reuses the same array: calls whose work overlaps on the
- * GPU (other streams or other host threads) race, so serialize them.  The call
- * returns once the fold has finished; a plan with no histories yet returns
+ * the array's device address (under a lock, so first calls from several host
+ * threads are safe), so make that first call before any stream capture begins
+ * on any thread.  Every call reuses the same array: calls whose work overlaps
+ * on the GPU (other streams or other host threads) race, so serialize them.
+ * The call is synchronous: it waits on `stream` for the fold and copies the
+ * stats to the host before it returns.  A plan with no histories yet returns
  * GPUMCD_ERR_STATE. */
 gpumcd_status gpumcd_plan_result_noalloc(gpumcd_ctx *ctx, int32_t plan_id, double threshold_frac,
                                          double *dose_out, double *sigma_out, void *stream,

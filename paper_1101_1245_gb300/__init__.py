@@ -127,6 +127,10 @@ SIGNATURES = {
     "gpumcd_poll": (_ST, [_CTX, _I32, C.POINTER(_I32)]),
     "gpumcd_wait": (_ST, [_CTX, _I32]),
     "gpumcd_plan_result": (_ST, [_CTX, _I32, _D, _P, _P, _P, C.POINTER(RunStats)]),
+    "gpumcd_plan_result_host": (_ST, [_CTX, _I32, _D, _P, _P, C.POINTER(RunStats)]),
+    "gpumcd_run_to_uncertainty": (_ST, [_CTX, _I32, C.POINTER(_I32), C.POINTER(_U64), C.POINTER(_U64), _D, _D,
+                                        _P, C.POINTER(_U64), C.POINTER(_D), C.POINTER(C.c_uint32),
+                                        C.POINTER(_D)]),
     "gpumcd_plan_histories": (_ST, [_CTX, _I32, C.POINTER(_U64)]),
     "gpumcd_plan_result_noalloc": (_ST, [_CTX, _I32, _D, _P, _P, _P, C.POINTER(RunStats)]),
     "gpumcd_memory": (_ST, [_CTX, C.POINTER(_U64), C.POINTER(_U64)]),
@@ -351,6 +355,37 @@ class Context:
                                           sigma_ptr or None, stream or None, C.byref(st)),
                "gpumcd_plan_result")
         return st.as_dict()
+
+    def plan_result_host(self, plan: int, threshold: float = 0.5, dose: Optional[np.ndarray] = None,
+                         sigma: Optional[np.ndarray] = None) -> dict:
+        """gpumcd_plan_result_host into caller-owned C-contiguous float64 host
+        arrays of nvox entries (for example views of pinned memory)."""
+        for a in (dose, sigma):
+            if a is not None and (a.dtype != np.float64 or not a.flags.c_contiguous):
+                raise ValueError("host outputs must be C-contiguous float64 arrays")
+        st = RunStats()
+        _check(self._L.gpumcd_plan_result_host(self.h, plan, threshold,
+                                               dose.ctypes.data if dose is not None else None,
+                                               sigma.ctypes.data if sigma is not None else None,
+                                               C.byref(st)), "gpumcd_plan_result_host")
+        return st.as_dict()
+
+    def run_to_uncertainty(self, plans: Sequence[int], first_histories: Sequence[int],
+                           max_histories: Sequence[int], target: float, threshold: float = 0.5,
+                           stream: int = 0) -> dict:
+        """gpumcd_run_to_uncertainty: the plans' total histories, final s, the
+        rounds run and the device time of their transport launches."""
+        k = len(plans)
+        ids = (_I32 * k)(*plans)
+        first = (_U64 * k)(*first_histories)
+        mx = (_U64 * k)(*max_histories)
+        h = (_U64 * k)()
+        s = (_D * k)()
+        r = C.c_uint32()
+        ms = _D()
+        _check(self._L.gpumcd_run_to_uncertainty(self.h, k, ids, first, mx, target, threshold, stream or None,
+                                                 h, s, C.byref(r), C.byref(ms)), "gpumcd_run_to_uncertainty")
+        return {"histories": list(h), "s_thr": list(s), "rounds": r.value, "transport_ms": ms.value}
 
     def plan_histories(self, plan: int) -> int:
         h = _U64()

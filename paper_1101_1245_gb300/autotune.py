@@ -19,7 +19,7 @@ from typing import Dict, List, Sequence, Tuple
 from . import ERR_INVALID_ARG, Context, GpumcdError
 
 # (block_threads, blocks_per_sm) shapes with a kernel variant behind them
-SHAPES: List[Tuple[int, int]] = [(512, 2), (384, 2), (256, 3), (512, 1)]
+SHAPES: List[Tuple[int, int]] = [(512, 2), (384, 2), (256, 3), (256, 4), (512, 1)]
 KNOBS: Dict[str, List[int]] = {
     "chunk": [16, 32, 64],
     "switch_high": [200, 320, 384],

@@ -1061,13 +1061,15 @@ gpumcd_status gpumcd_plan_result(gpumcd_ctx *c, int32_t plan_id, double thr, dou
     Plan &p = it->second;
     const Phantom &ph = c->phantoms.at(p.phantom);
     const uint64_t nvox = ph.nvox;
-    // scratch: [dose | sigma] when the caller passes NULL, then [n_b (64) | dmax | sum | count | esum]
-    const size_t need = (size_t)nvox * 16 + 64 * 8 + 64;
+    // scratch: [dose | sigma] when the caller passes NULL, then [n_b (64) | dmax | sum | count | esum],
+    // then the s_thr reduction's per-block partials
+    const size_t need = (size_t)nvox * 16 + 64 * 8 + 64 + (size_t)sthr_blocks(nvox, c->n_sm) * 16;
     ST(dev_alloc(c, c->fold_tmp, need));
     double *tdose = (double *)c->fold_tmp.p;
     double *tsig = tdose + nvox;
     double *nb = tsig + nvox;
     unsigned long long *red = (unsigned long long *)(nb + 64);
+    void *sthr_part = red + 8;
     double *ddose = dose ? dose : tdose;
     double *dsig = sigma ? sigma : tsig;
     double h_nb[64] = {0};
@@ -1079,7 +1081,7 @@ gpumcd_status gpumcd_plan_result(gpumcd_ctx *c, int32_t plan_id, double thr, dou
     if (N > 0) {
         CK(launch_fold((const unsigned long long *)p.tally.p, (const uint32_t *)ph.vox.p, nvox, (int)p.W, h_nb,
                        (double)N, inv_vol, ddose, dsig, red, red + 3, c->n_sm, s));
-        CK(launch_sthr(ddose, dsig, nvox, red, thr, (double *)(red + 1), red + 2, c->n_sm, s));
+        CK(launch_sthr(ddose, dsig, nvox, red, thr, (double *)(red + 1), red + 2, sthr_part, c->n_sm, s));
     } else {
         CK(cudaMemsetAsync(ddose, 0, nvox * 8, s));
         CK(cudaMemsetAsync(dsig, 0, nvox * 8, s));
@@ -1140,6 +1142,105 @@ gpumcd_status gpumcd_plan_result_noalloc(gpumcd_ctx *c, int32_t plan_id, double 
         memcpy(&stats->d_max_gy, &res[0], 8);
         memcpy(&stats->s_thr, &res[2], 8);
     }
+    return GPUMCD_OK;
+}
+
+gpumcd_status gpumcd_plan_result_host(gpumcd_ctx *c, int32_t plan_id, double thr, double *dose, double *sigma,
+                                      gpumcd_run_stats *stats) {
+    if (!c) return GPUMCD_ERR_INVALID_ARG;
+    auto it = c->plans.find(plan_id);
+    if (it == c->plans.end()) return GPUMCD_ERR_NOT_FOUND;
+    // the fold writes [dose | sigma] into the context's fold scratch, then both
+    // arrays come back in two copies on the context's stream
+    ST(gpumcd_plan_result(c, plan_id, thr, nullptr, nullptr, nullptr, stats));
+    const uint64_t nvox = c->phantoms.at(it->second.phantom).nvox;
+    const double *td = (const double *)c->fold_tmp.p;
+    if (dose) CK(cudaMemcpyAsync(dose, td, nvox * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (sigma) CK(cudaMemcpyAsync(sigma, td + nvox, nvox * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return GPUMCD_OK;
+}
+
+gpumcd_status gpumcd_run_to_uncertainty(gpumcd_ctx *c, int32_t n_plans, const int32_t *ids,
+                                        const uint64_t *first, const uint64_t *max_hist, double target,
+                                        double thr, void *stream, uint64_t *hist_out, double *s_out,
+                                        uint32_t *rounds_out, double *transport_ms_out) {
+    if (!c || n_plans < 1 || n_plans > GPUMCD_MAX_PLANS_PER_RUN || !ids || !first || !max_hist) return GPUMCD_ERR_INVALID_ARG;
+    if (!(target > 0.0) || !(thr >= 0.0 && thr <= 1.0)) return GPUMCD_ERR_INVALID_ARG;
+    std::vector<uint64_t> done(n_plans), goal(n_plans);
+    std::vector<double> s(n_plans, INFINITY);
+    std::vector<uint32_t> W(n_plans);
+    for (int i = 0; i < n_plans; ++i) {
+        auto it = c->plans.find(ids[i]);
+        if (it == c->plans.end()) return GPUMCD_ERR_NOT_FOUND;
+        for (int j = 0; j < i; ++j)
+            if (ids[j] == ids[i]) return GPUMCD_ERR_INVALID_ARG;
+        if (it->second.inflight > 0 || it->second.failed) return GPUMCD_ERR_STATE;
+        if (first[i] < 1 || max_hist[i] < first[i] || max_hist[i] > (1ull << 32)) return GPUMCD_ERR_INVALID_ARG;
+        done[i] = it->second.hist_done;
+        W[i] = it->second.W;
+        goal[i] = done[i] + first[i];
+    }
+    std::vector<char> active(n_plans, 1);
+    uint32_t rounds = 0;
+    double transport_ms = 0.0;
+    for (;;) {
+        // this round: every active plan runs up to its goal, in whole multiples of
+        // its W batches (so the batches stay equal), within its history cap
+        std::vector<int32_t> rid;
+        std::vector<uint64_t> rn;
+        for (int i = 0; i < n_plans; ++i) {
+            if (!active[i]) continue;
+            const uint64_t diff = goal[i] > done[i] ? goal[i] - done[i] : 0;
+            uint64_t n = std::max<uint64_t>(W[i], (diff + W[i] - 1) / W[i] * W[i]);
+            n = std::min<uint64_t>(n, max_hist[i] - done[i]);
+            if (n == 0) {
+                active[i] = 0;
+                continue;
+            }
+            rid.push_back(ids[i]);
+            rn.push_back(n);
+        }
+        if (rid.empty()) break;
+        // a round is one sequence per particle type: its device time is the
+        // growth of one plan's transport time per type
+        double before[2] = {-1.0, -1.0};
+        int32_t probe[2] = {-1, -1};
+        for (int32_t id : rid) {
+            const Plan &pl = c->plans.at(id);
+            const int t = pl.particle == GPUMCD_ELECTRON ? 1 : 0;
+            if (probe[t] < 0) {
+                probe[t] = id;
+                before[t] = pl.acc.transport_ms;
+            }
+        }
+        ST(gpumcd_run(c, (int32_t)rid.size(), rid.data(), rn.data(), stream));
+        for (int t = 0; t < 2; ++t)
+            if (probe[t] >= 0) transport_ms += c->plans.at(probe[t]).acc.transport_ms - before[t];
+        ++rounds;
+        for (size_t r = 0, i = 0; r < rid.size(); ++r) {
+            while (ids[i] != rid[r]) ++i;
+            done[i] += rn[r];
+            gpumcd_run_stats st{};
+            ST(gpumcd_plan_result(c, ids[i], thr, nullptr, nullptr, stream, &st));
+            s[i] = st.s_thr > 0.0 ? st.s_thr : INFINITY;
+            if (s[i] <= target || done[i] >= max_hist[i]) {
+                active[i] = 0;
+            } else {
+                // s falls as 1/sqrt(N): the count expected to reach the target,
+                // with 5% to spare, and at least 10% more than now
+                const double want = std::max((double)done[i] * (s[i] / target) * (s[i] / target) * 1.05,
+                                             (double)done[i] * 1.1);
+                goal[i] = want >= (double)max_hist[i] ? max_hist[i] : (uint64_t)want;
+            }
+        }
+    }
+    for (int i = 0; i < n_plans; ++i) {
+        if (hist_out) hist_out[i] = done[i];
+        if (s_out) s_out[i] = s[i];
+    }
+    if (rounds_out) *rounds_out = rounds;
+    if (transport_ms_out) *transport_ms_out = transport_ms;
     return GPUMCD_OK;
 }
 

@@ -27,9 +27,11 @@ cudaError_t launch_spectrum(const double *edges, const double *w, int n, float *
 cudaError_t launch_fold(const unsigned long long *tally, const uint32_t *vox, uint64_t nvox, int W,
                         const double *n_b, double n_tot, double inv_vol, double *dose, double *sigma,
                         unsigned long long *dmax_bits, unsigned long long *dep_sum, int n_sm, cudaStream_t s);
+// Blocks of the s_thr reduction for nvox voxels: its partials take 16 bytes each.
+int sthr_blocks(uint64_t nvox, int n_sm);
 cudaError_t launch_sthr(const double *dose, const double *sigma, uint64_t nvox,
                         const unsigned long long *dmax_bits, double thr, double *sum,
-                        unsigned long long *count, int n_sm, cudaStream_t s);
+                        unsigned long long *count, void *part, int n_sm, cudaStream_t s);
 cudaError_t launch_sum_u64(const unsigned long long *a, uint64_t n, unsigned long long *out, int n_sm,
                            cudaStream_t s);
 cudaError_t launch_fold_noalloc(int device, const unsigned long long *tally, const uint32_t *vox, uint64_t nvox,

@@ -72,10 +72,16 @@ def test_autotune_changes_speed_not_results():
 
 
 def test_served_results_equal_alone_reruns():
+    """Request 3 is a spectrum grouped by energy (§IV): its strata follow from
+    the history index, so it too equals its alone rerun under another split."""
     from paper_1101_1245_gb300.serve import DoseRequest, Server
     ctx = make_ctx()
     specs = _specs(6, seed=46)
     phantoms, pids, srcs = _setup(ctx, specs)
+    edges, w = W.synthetic_6mv_spectrum(n_bins=64)
+    srcs[3] = W.Source(specs[3].particle, W.BEAM_SQUARE, center_cm=srcs[3].center_cm,
+                       field_cm=srcs[3].field_cm, spectrum_edges=edges, spectrum_weights=w,
+                       energy_grouping=W.ENERGY_GROUPED)
     srv = Server(ctx, hbm_budget=8 << 30, target=0.05, round_histories=300_000,
                  first_chunk=20_000, keep_dose=True)
     for i, (pid, src, sp) in enumerate(zip(pids, srcs, specs)):
@@ -199,3 +205,42 @@ def test_graph_launches_equal_direct_launches():
         assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
         assert x[2]["histories"] == y[2]["histories"]
         assert y[2]["e_deposited"] + y[2]["e_escaped"] + y[2]["e_rest"] == y[2]["e_incident"]
+
+
+def test_run_to_uncertainty_batched_equals_plans_alone():
+    """gpumcd_run_to_uncertainty (§II.D: run until s_0.5 reaches the target):
+    six uneven plans together and each plan by itself take the same rounds of
+    histories, stop at or below the target, and end with the same tallies bit
+    for bit; results through host outputs equal the device ones."""
+    import torch
+    ctx = make_ctx()
+    specs = _specs(6, seed=49)
+    phantoms, pids, srcs = _setup(ctx, specs)
+    first = [sp.n_histories for sp in specs]
+    cap = [3_000_000] * len(specs)
+    together = [ctx.plan_open(pid, src, sp.seed, 16) for pid, src, sp in zip(pids, srcs, specs)]
+    res = ctx.run_to_uncertainty(together, first, cap, 0.05)
+    assert res["rounds"] >= 2
+    for i in range(len(specs)):
+        h, s = res["histories"][i], res["s_thr"][i]
+        assert h % 16 == 0 and first[i] <= h <= cap[i]
+        assert s <= 0.05 or h == cap[i]
+        alone = ctx.plan_open(pids[i], srcs[i], specs[i].seed, 16)
+        one = ctx.run_to_uncertainty([alone], [first[i]], [cap[i]], 0.05)
+        assert one["histories"] == [h] and one["s_thr"] == [s]
+        a, b = _dose(ctx, together[i], phantoms[i].nvox), _dose(ctx, alone, phantoms[i].nvox)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        assert a[2]["e_deposited"] + a[2]["e_escaped"] + a[2]["e_rest"] == a[2]["e_incident"]
+        hd = torch.empty(phantoms[i].nvox, dtype=torch.float64).pin_memory().numpy()
+        hs = np.empty(phantoms[i].nvox, dtype=np.float64)
+        st = ctx.plan_result_host(alone, 0.5, hd, hs)
+        assert np.array_equal(hd, a[0]) and np.array_equal(hs, a[1])
+        assert st["histories"] == h
+        ctx.plan_close(alone)
+    with pytest.raises(g.GpumcdError) as e:
+        ctx.run_to_uncertainty([together[0]], [0], [10], 0.05)
+    assert e.value.status == g.ERR_INVALID_ARG
+    with pytest.raises(g.GpumcdError) as e:
+        ctx.run_to_uncertainty([together[0], together[0]], [16, 16], [32, 32], 0.05)
+    assert e.value.status == g.ERR_INVALID_ARG
+    ctx.close()
