@@ -69,7 +69,7 @@ class SourceC(C.Structure):
                 ("n_spec", C.c_int32), ("spec_edges", C.POINTER(C.c_double)),
                 ("spec_weights", C.POINTER(C.c_double)), ("cx", C.c_double), ("cy", C.c_double),
                 ("field", C.c_double), ("n_phsp", C.c_int32), ("phsp", C.POINTER(C.c_double)),
-                ("group", C.c_int32), ("run_begin", C.c_uint64), ("run_n", C.c_uint64)]
+                ("group", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -190,9 +190,9 @@ def phantom(ph, keep: _Keep) -> PhantomC:
                     rho.ctypes.data_as(C.POINTER(C.c_float)))
 
 
-def source(src, keep: _Keep, run=(0, 0)) -> SourceC:
-    """The C source; run = (first history, histories) of the run a grouped
-    spectrum is stratified over."""
+def source(src, keep: _Keep) -> SourceC:
+    """The C source (a grouped spectrum's strata follow from the history
+    index alone, see oracle.h)."""
     s = SourceC()
     s.particle = src.particle
     s.beam = src.beam
@@ -210,7 +210,6 @@ def source(src, keep: _Keep, run=(0, 0)) -> SourceC:
         s.n_spec = 0
     grouped = getattr(src, "energy_grouping", 0) == 1
     s.group = 1 if grouped and src.spectrum_edges is not None else 0
-    s.run_begin, s.run_n = int(run[0]), int(run[1])
     ps = getattr(src, "phase_space", None)
     if ps is not None:
         a = np.ascontiguousarray(ps, dtype=np.float64).reshape(-1, 7)
@@ -255,14 +254,13 @@ class OracleResult:
         return s * MEV_PER_G_TO_GY
 
 
-def simulate_range(mats, phys, ph, src, h0: int, h1: int, seed: int, flags: int = 0, run=None):
-    """One single-threaded oracle call over histories [h0, h1), part of the run
-    `run` = (first history, histories); by default the range itself."""
+def simulate_range(mats, phys, ph, src, h0: int, h1: int, seed: int, flags: int = 0):
+    """One single-threaded oracle call over histories [h0, h1)."""
     L = lib()
     keep = _Keep()
     marr = materials(mats)
     pc = phantom(ph, keep)
-    sc = source(src, keep, run if run is not None else (h0, h1 - h0))
+    sc = source(src, keep)
     pp = physics(phys)
     s1 = np.zeros(ph.nvox, dtype=np.float64)
     s2 = np.zeros(ph.nvox, dtype=np.float64)
@@ -275,8 +273,8 @@ def simulate_range(mats, phys, ph, src, h0: int, h1: int, seed: int, flags: int 
 
 
 def _worker(args):
-    mats, phys, ph, src, h0, h1, seed, flags, run = args
-    return simulate_range(mats, phys, ph, src, h0, h1, seed, flags, run)
+    mats, phys, ph, src, h0, h1, seed, flags = args
+    return simulate_range(mats, phys, ph, src, h0, h1, seed, flags)
 
 
 def simulate(mats, phys, ph, src, n_histories: int, seed: int, flags: int = 0,
@@ -296,8 +294,7 @@ def simulate(mats, phys, ph, src, n_histories: int, seed: int, flags: int = 0,
         import multiprocessing as mp
 
         cuts = np.linspace(hist_begin, hist_begin + n_histories, processes + 1).astype(np.int64)
-        run = (hist_begin, n_histories)
-        jobs = [(mats, phys, ph, src, int(cuts[i]), int(cuts[i + 1]), seed, flags, run)
+        jobs = [(mats, phys, ph, src, int(cuts[i]), int(cuts[i + 1]), seed, flags)
                 for i in range(processes)]
         ctx = mp.get_context("spawn")
         with ctx.Pool(processes) as pool:
@@ -325,8 +322,7 @@ def simulate_parts(mats, phys, ph, src, n_histories: int, seed: int, parts: int,
         sub = np.linspace(cuts[i], cuts[i + 1], per_part + 1).astype(np.int64)
         for j in range(per_part):
             if sub[j + 1] > sub[j]:
-                jobs.append((mats, phys, ph, src, int(sub[j]), int(sub[j + 1]), seed, flags,
-                             (int(cuts[i]), int(cuts[i + 1] - cuts[i]))))
+                jobs.append((mats, phys, ph, src, int(sub[j]), int(sub[j + 1]), seed, flags))
                 owner.append(i)
     with mp.get_context("spawn").Pool(max(1, min(processes, len(jobs)))) as pool:
         outs = pool.map(_worker, jobs)
@@ -341,13 +337,12 @@ def simulate_parts(mats, phys, ph, src, n_histories: int, seed: int, parts: int,
     return res
 
 
-def primary_energies(src, h0: int, h1: int, seed: int, run=None) -> np.ndarray:
+def primary_energies(src, h0: int, h1: int, seed: int) -> np.ndarray:
     """The primary energies (MeV) of histories [h0, h1), drawn as the
-    transport draws them; run = (first history, histories) of a grouped
-    spectrum's run, by default the range itself."""
+    transport draws them."""
     L = lib()
     keep = _Keep()
-    sc = source(src, keep, run if run is not None else (h0, h1 - h0))
+    sc = source(src, keep)
     out = np.zeros(h1 - h0, dtype=np.float64)
     if L.om_primary_energies(C.byref(sc), h0, h1, seed, out.ctypes.data_as(_DP)) != 0:
         raise RuntimeError("om_primary_energies failed")
@@ -359,7 +354,7 @@ def first_interaction_z(mats, phys, ph, src, n: int, seed: int):
     keep = _Keep()
     marr = materials(mats)
     pc = phantom(ph, keep)
-    sc = source(src, keep, (0, n))
+    sc = source(src, keep)
     pp = physics(phys)
     z = np.zeros(n, dtype=np.float64)
     nf = C.c_uint64(0)

@@ -734,9 +734,19 @@ static void make_primary(ctx_t *c, const om_source *src, const double *cdf, uint
     p->u[1] = 0.0;
     p->u[2] = 1.0;
     if (src->n_spec > 0 && src->group) {
-        /* energy grouping (§IV): stratum h - run_begin of run_n, from the top */
+        /* energy grouping (§IV): stratum s of the aligned block of 2^16 histories
+         * holding h, rotated by the block's own draw (see om_source) */
         const double u = uniform(s);
-        const double z = 1.0 - ((double)(h - src->run_begin) + u) / (double)src->run_n;
+        const uint32_t k = (uint32_t)(h >> 16), j = (uint32_t)(h & 0xFFFFu);
+        const uint32_t ctr[4] = {0u, 0u, 0u, k};
+        const uint32_t key[2] = {(uint32_t)c->seed, (uint32_t)(c->seed >> 32)};
+        uint32_t w[4];
+        om_philox4x32_10(ctr, key, w);
+        const uint32_t chunk = j >> 6;
+        uint32_t rev = 0;
+        for (int b = 0; b < 10; ++b) rev |= ((chunk >> b) & 1u) << (9 - b);
+        const uint32_t stratum = (64u * rev + (j & 63u) + (w[0] & 0xFFFFu)) & 0xFFFFu;
+        const double z = ((double)stratum + u) / 65536.0;
         p->E = spectrum_at(src->n_spec, src->spec_edges, cdf, z);
     } else {
         p->E = src->n_spec > 0 ? sample_spectrum(s, src->n_spec, src->spec_edges, cdf) : src->energy;
@@ -751,9 +761,6 @@ int32_t om_simulate(const om_material *mats, int32_t n_mat, const om_physics *ph
                     uint64_t hist_end, uint64_t seed, uint32_t flags, double *sum_e,
                     double *sum_e2, om_stats *stats) {
     if (validate(mats, n_mat, phys, ph, src) != 0 || !sum_e || !sum_e2 || !stats) return -1;
-    if (src->group && src->n_spec > 0 &&
-        (hist_begin < src->run_begin || hist_end > src->run_begin + src->run_n || src->run_n == 0))
-        return -1;
     ctx_t c;
     if (ctx_setup(&c, mats, n_mat, phys, ph, seed, flags, stats) != 0) {
         ctx_free(&c);
@@ -802,7 +809,6 @@ int32_t om_first_interaction_z(const om_material *mats, int32_t n_mat, const om_
                                const om_phantom *ph, const om_source *src, int64_t n,
                                uint64_t seed, double *z_out, uint64_t *n_fict_out) {
     if (validate(mats, n_mat, phys, ph, src) != 0 || src->particle != 0) return -1;
-    if (src->group && src->n_spec > 0 && (src->run_begin != 0 || src->run_n < (uint64_t)n)) return -1;
     om_stats st;
     memset(&st, 0, sizeof st);
     ctx_t c;
@@ -863,10 +869,7 @@ void om_sample_ms(double g1, int64_t n, uint64_t seed, double *mu_out) {
 
 int32_t om_primary_energies(const om_source *src, uint64_t hist_begin, uint64_t hist_end,
                             uint64_t seed, double *e_out) {
-    if (!src || !e_out || src->beam == 2 || src->n_spec < 0) return -1;
-    if (src->group && src->n_spec > 0 &&
-        (hist_begin < src->run_begin || hist_end > src->run_begin + src->run_n || src->run_n == 0))
-        return -1;
+    if (!src || !e_out || src->beam == 2 || src->n_spec < 0 || hist_end < hist_begin) return -1;
     ctx_t c;
     memset(&c, 0, sizeof c);
     c.seed = seed;

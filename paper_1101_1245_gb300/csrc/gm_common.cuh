@@ -100,7 +100,7 @@ struct __align__(16) PlanDev {
     uint32_t e_src_q, n_phsp;     // n_phsp: phase-space records (spec holds them)
     unsigned long long hist_base;  // first history of this launch
     unsigned long long n_hist;     // histories in this launch
-    uint32_t e_group, pad_g;       // e_group: spectrum stratified over this launch's histories
+    uint32_t e_group, pad_g;       // e_group: spectrum stratified over aligned blocks of 2^16 histories
 };
 static_assert(sizeof(PlanDev) == 160, "the plan table in shared memory keeps its size");
 

@@ -355,7 +355,7 @@ __device__ __forceinline__ float sample_spectrum(const PlanDev &P, float z) {
 // parallel beam entering through z = 0 along +z; with PHSP, a phase-space
 // plan's primary is record h mod n as listed (the first draw is still taken,
 // so the draw counter starts where the beams' does), and a grouped spectrum
-// is sampled stratified over the launch's histories.
+// is sampled stratified over aligned blocks of 2^16 histories.
 template <bool PHSP>
 __device__ __forceinline__ uint32_t make_primary(Lane &p, const PlanDev &P, uint32_t plan, uint64_t h) {
     p.hist = (uint32_t)h;
@@ -390,11 +390,17 @@ __device__ __forceinline__ uint32_t make_primary(Lane &p, const PlanDev &P, uint
     p.uz = 1.0f;
     float zq = u01(r.z);
     if (PHSP && P.e_group) {
-        // energy grouping (§IV): history j of the launch's n draws its quantile
-        // from stratum j, counted down from the top of the spectrum
-        const float inv_n = 1.0f / (float)P.n_hist;
-        const float j = (float)(h - P.hist_base);
-        zq = fminf(fmaxf(fmaf(-zq, inv_n, fmaf(-j, inv_n, 1.0f)), 0.0f), 1.0f);
+        // energy grouping (§IV): history j of the aligned block k of 2^16 takes
+        // stratum (64 bitrev10(j / 64) + j mod 64 + r_k) mod 2^16, r_k the
+        // block's own draw (counter (0, 0, 0, k): lineage 0 belongs to no
+        // particle).  64 consecutive histories take consecutive strata, a block
+        // takes each stratum once, and over r_k every quantile is uniform, so
+        // the energy is unbiased for any history count and depends on h alone.
+        // The quantile (s + u) / 2^16 is exact to 2^-24, 1/256 of a stratum.
+        const uint32_t k = (uint32_t)(h >> 16), j = (uint32_t)h & 0xFFFFu;
+        const uint4 rb = philox4x32_10(make_uint4(0u, 0u, 0u, k), make_uint2(P.key_lo, P.key_hi));
+        const uint32_t st = ((__brev(j >> 6) >> 22) * 64u + (j & 63u) + (rb.x & 0xFFFFu)) & 0xFFFFu;
+        zq = fminf(((float)st + zq) * (1.0f / 65536.0f), 1.0f);
     }
     p.E = P.n_spec > 0 ? __float2uint_rn(sample_spectrum(P, zq) * kInvQf) : P.e_src_q;
     p.act = true;

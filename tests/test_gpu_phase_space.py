@@ -173,25 +173,26 @@ def _mean_energy(edges, w):
 
 
 def test_grouped_spectrum_parity_and_strata(ctx):
-    """A grouped 6 MV-like photon spectrum (one draw per stratum of each run,
-    highest energies first) against the oracle's grouped run: the dose within
-    3 sigma, an exact ledger, and an incident energy that only stratification
-    gives - within the spectrum's width of n times its mean energy on both
-    sides, where iid draws scatter by ~400 MeV at this n."""
+    """A grouped 6 MV-like photon spectrum (one draw per stratum of each
+    aligned block of 2^16 histories) against the oracle's grouped run: the
+    dose within 3 sigma, an exact ledger, and, over two whole blocks, an
+    incident energy that only stratification gives - within a few widths of
+    the spectrum of n times its mean energy on both sides, where iid draws
+    scatter by ~450 MeV at this n."""
     edges, w = W.synthetic_6mv_spectrum()
     ph = W.z_slabs((32, 32, 48), 0.5, [(3.0, W.MAT_WATER, 1.0), (2.0, W.MAT_BONE, 1.85),
                                        (6.0, W.MAT_LUNG, 0.26), (1e9, W.MAT_WATER, 1.0)])
     src = W.Source(W.PHOTON, W.BEAM_SQUARE, center_cm=(8.0, 8.0), field_cm=8.0, spectrum_edges=edges,
                    spectrum_weights=w, energy_grouping=W.ENERGY_GROUPED)
-    n = 100_000
+    n = 2 * 65536
     plan = W.Plan("grouped_spectrum", ph, src, n, 43)
     gpu = run_gpu(ctx, plan)
     ora = run_oracle(plan)
     assert ledger_exact(gpu.stats)
     width = float(edges[-1] - edges[0])
     want = n * _mean_energy(edges, w)
-    assert abs(gpu.stats["e_incident"] * Q - want) <= 2.0 * width
-    assert abs(ora.stats["e_incident"] - want) <= width + 1e-6
+    assert abs(gpu.stats["e_incident"] * Q - want) <= 3.0 * width
+    assert abs(ora.stats["e_incident"] - want) <= 2.0 * width + 1e-6
     do, so = ora.dose_gy(ph), ora.sigma_gy(ph)
     mask = do > 0.1 * do.max()
     assert mask.sum() > 100

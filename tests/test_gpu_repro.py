@@ -1,5 +1,6 @@
 """Scheduling independence: the dose tally is bit-identical whatever the launch
-shape, the history split, the warp-aggregation mode or the overflow path,
+shape, the history split (energy-grouped spectra included), the
+warp-aggregation mode or the overflow path,
 because each particle's random stream depends only on (seed, history,
 lineage, draw) and energies are integers."""
 import numpy as np
@@ -38,10 +39,21 @@ EVENT_KEYS = ("e_incident", "e_deposited", "e_escaped", "e_rest", "n_photon_even
               "n_compton", "n_photo", "n_pair", "n_electron_steps", "n_hard_real", "n_hard_fict",
               "n_moller", "n_brem", "n_photons", "n_electrons", "n_sampler_capped")
 
+_EDGES, _W = W.synthetic_6mv_spectrum(n_bins=64)
 SOURCES = {
     "electron": W.Source(W.ELECTRON, W.BEAM_SQUARE, energy=12.0, center_cm=(6.0, 5.0), field_cm=4.0),
     "photon": W.Source(W.PHOTON, W.BEAM_SQUARE, energy=15.0, center_cm=(6.0, 5.0), field_cm=4.0),
+    # a spectrum grouped by energy (§IV): its strata follow from the history index
+    "grouped": W.Source(W.PHOTON, W.BEAM_SQUARE, center_cm=(6.0, 5.0), field_cm=4.0,
+                        spectrum_edges=_EDGES, spectrum_weights=_W, energy_grouping=W.ENERGY_GROUPED),
 }
+
+
+def _phsp_kernel_accepts(launch) -> bool:
+    """A grouped spectrum runs the phase-space kernel: at most 2 CTAs per SM,
+    no profile or aggregation flag, refill at every pass."""
+    return (launch.get("blocks_per_sm", 2) <= 2 and launch.get("refill_period", 1) == 1
+            and not launch.get("flags", 0) & (g.LAUNCH_WARP_AGGREGATE | g.LAUNCH_PROFILE))
 
 
 @pytest.fixture(scope="module")
@@ -53,7 +65,7 @@ def reference():
     return ph, out
 
 
-@pytest.mark.parametrize("kind", ["electron", "photon"])
+@pytest.mark.parametrize("kind", ["electron", "photon", "grouped"])
 @pytest.mark.parametrize("launch", [
     dict(),
     dict(block_threads=256, blocks_per_sm=2),
@@ -69,6 +81,8 @@ def reference():
     dict(refill_period=g.REFILL_WHEN_EMPTY),
 ])
 def test_bit_identical_across_launch_shapes(reference, kind, launch):
+    if kind == "grouped" and not _phsp_kernel_accepts(launch):
+        pytest.skip("outside the phase-space kernel's launch restrictions")
     ph, out = reference
     ctx = make_ctx(**launch)
     d, s, st = _dose(ctx, ph, SOURCES[kind], 40_000, 99)
@@ -84,10 +98,11 @@ def test_bit_identical_across_launch_shapes(reference, kind, launch):
     assert st["n_moller"] + st["n_brem"] == st["n_hard_real"]
 
 
-@pytest.mark.parametrize("kind", ["electron", "photon"])
+@pytest.mark.parametrize("kind", ["electron", "photon", "grouped"])
 @pytest.mark.parametrize("flags", [0, g.LAUNCH_GRAPH])
 def test_split_runs_equal_one_run(reference, kind, flags):
-    """Also replays one captured graph with new kernel arguments per run."""
+    """Also replays one captured graph with new kernel arguments per run.  A
+    grouped spectrum included: its strata depend on the history index alone."""
     ph, out = reference
     ctx = make_ctx(flags=flags)
     d, s, st = _dose(ctx, ph, SOURCES[kind], 40_000, 99, splits=(10_000, 17_000, 13_000))
