@@ -1,6 +1,7 @@
 """FP32 transport (the CUDA path) against the FP64 oracle, per workload: the
-dose-error report for the C1-C3 configurations.  Needs a GPU; run from the
-repository root:
+dose-error report for every configuration - C1 to C3, four plans of the
+batched workload (C4) and three requests of the served stream (C5, each on
+its resident phantom).  Needs a GPU; run from the repository root:
 
     python tests/report_fp_error.py [--out FILE]
 
@@ -20,7 +21,7 @@ sign.  One JSON object per configuration:
   region_bias, _se     relative difference of the region-mean dose, with its
                        standard error from the spread of the K parts (which
                        carries the voxel-to-voxel correlation)
-  slabs                for layered phantoms, the same per material layer inside
+  slabs                for z-layered phantoms, the same per material layer inside
                        the central 8 x 8 cm
   gamma_2_2            2%/2 mm gamma pass rate (C1, C2)
   dep_frac_gpu/_ora    deposited / incident energy, K-part mean and its standard error
@@ -41,17 +42,33 @@ if ROOT not in sys.path:
 
 K = 8  # independent parts on each side
 CASES = [
-    # name, plan factory, GPU histories, oracle histories, gamma
+    # name, plan factory, its argument, GPU histories, oracle histories, gamma
     ("c1_water32_2MeV_photon_pencil", "config1", None, 4_000_000, 1_000_000, True),
     ("c2_water128_15MeV_electron", "config2", "electron", 1_000_000, 200_000, True),
     ("c2_water128_15MeV_photon", "config2", "photon", 4_000_000, 400_000, True),
     ("c3_slabs256_6MV_spectrum", "config3", None, 10_000_000, 240_000, False),
+    # plans of the batched workload with phantoms small enough for the oracle
+    ("c4_plan24_electron_64cube", "config4", 24, 4_000_000, 400_000, False),
+    ("c4_plan14_electron_64cube", "config4", 14, 4_000_000, 400_000, False),
+    ("c4_plan07_photon_70cube", "config4", 7, 8_000_000, 800_000, False),
+    ("c4_plan58_photon_73cube", "config4", 58, 8_000_000, 800_000, False),
+    # requests of the served stream: the request's beam on phantom i mod 64
+    ("c5_request07_electron", "config5", 7, 4_000_000, 400_000, False),
+    ("c5_request14_photon", "config5", 14, 8_000_000, 800_000, False),
+    ("c5_request24_electron", "config5", 24, 4_000_000, 400_000, False),
 ]
 
 
-def _plan(W, factory, particle):
+def _plan(W, factory, arg):
     if factory == "config2":
-        return W.config2(W.ELECTRON if particle == "electron" else W.PHOTON)
+        return W.config2(W.ELECTRON if arg == "electron" else W.PHOTON)
+    if factory == "config4":
+        return W.config4()[arg].plan()
+    if factory == "config5":
+        sp = W.config5()[arg].spec
+        ph = W.config4()[arg % 64].phantom()
+        return W.Plan(f"c5_request{arg}", ph, W.square_field(sp.particle, sp.energy, ph, sp.field_cm),
+                      sp.n_histories, sp.seed)
     return getattr(W, factory)()
 
 
@@ -119,7 +136,8 @@ def compare(plan, sel, dg, sg, do, so, gamma, g_parts, o_parts):
     nx, ny, nz = ph.dims
     mats = ph.mat[:, ny // 2, nx // 2]
     bounds = [0] + [k for k in range(1, nz) if mats[k] != mats[k - 1]] + [nz]
-    if len(bounds) > 2:
+    layered = all(np.all(ph.mat[k] == ph.mat[k].flat[0]) for k in range(nz))
+    if layered and len(bounds) > 2:
         h = int(round(4.0 / ph.voxel_cm[0]))
         c = nx // 2
         slabs = []

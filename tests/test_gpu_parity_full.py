@@ -9,8 +9,10 @@ sizes the comparisons use what holds at any size:
   average taken from K independent sub-runs on each side (neighbouring voxels
   are correlated, so per-voxel sigmas do not add up);
 - the exact integer energy ledger.
-C1 is small enough to run both sides at 1e6 histories: there the gamma index
-(2%/2 mm, voxels above 20% of D_max) must pass for >= 98% of voxels.
+Where the oracle can reach a reference noise under 1% of D_max in the
+high-dose region, the gamma index (2%/2 mm, voxels above 20% of D_max) must
+pass for >= 98% of voxels: C1 with both sides at 4e6 histories, and the C2
+beams on the paper's own 64^3 grid of 0.5 cm voxels.
 """
 import numpy as np
 import pytest
@@ -152,3 +154,30 @@ def test_c3_full_size_slabs_spectrum(ctx):
         g_m, o_m = slab(gd), slab(od)
         se = np.sqrt(g_m.var(ddof=1) / len(g_m) + o_m.var(ddof=1) / len(o_m))
         assert abs(g_m.mean() - o_m.mean()) <= 3.5 * se, (z0, z1, g_m.mean(), o_m.mean(), se)
+
+
+@pytest.mark.parametrize("particle,n_gpu,n_ora", [(W.ELECTRON, 30_000_000, 6_000_000),
+                                                  (W.PHOTON, 180_000_000, 36_000_000)])
+def test_c2_beams_gamma_on_the_paper_grid(ctx, particle, n_gpu, n_ora):
+    """The timing-case beams (15 MeV, 10 x 10 cm^2) on the paper's own grid for
+    its gamma comparisons, 64^3 water voxels of 0.5 cm (GPUMCD §III.A, Geom1):
+    gamma 2% / 2 mm over voxels above 20% of D_max passes for >= 98% of them,
+    with the oracle as the reference.  The oracle runs enough histories that its
+    own noise in the high-dose region is under 0.8% of D_max (the gamma index
+    has no term for the reference's noise: at 1.2-1.5% noise a flawless
+    evaluation would fail ~10% of the flat high-dose voxels), the GPU five
+    times more."""
+    plan = W.config2(particle, n=64, voxel_cm=0.5)
+    ph = plan.phantom
+    gd, gs, gst = _gpu_runs(ctx, plan, n_gpu, k=1, seed0=3)
+    assert ledger_exact(gst[0])
+    ora = oracle.simulate(W.MATERIALS, W.DEFAULT_PHYSICS, ph, plan.source, n_ora, 91,
+                          processes=host_cores())
+    do, so = ora.dose_gy(ph), ora.sigma_gy(ph)
+    high = do > 0.5 * do.max()
+    noise = float(np.median(so[high] / do.max()))
+    dg, sg = gd[0], gs[0]
+    rate = gamma_pass_rate(do.reshape(64, 64, 64), dg.reshape(64, 64, 64), (5.0, 5.0, 5.0))
+    assert noise < 0.008, (noise, rate)
+    assert three_sigma_pass_rate(dg, sg, do, so, do > 0.1 * do.max()) >= 0.99
+    assert rate >= 0.98, (rate, noise)
