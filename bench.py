@@ -1,11 +1,25 @@
 #!/usr/bin/env python
-"""Benchmark: histories/s of the coupled photon-electron transport on the
-paper's timing workload (GPUMCD §II.D / Table "resabsexec"): separate 15 MeV
-10x10 cm^2 parallel beams of 1e6 electrons and 4e6 photons on a 128^3 water
-phantom at 0.25 cm.  One step = both beams, each run from a zeroed tally to
-its FP64 dose and uncertainty on the device.
+"""Benchmark: histories/s at 1% dose uncertainty, plain vs batched vs served,
+with p50/p99 request latency (GPUMCD §II.D: the uncertainty s over voxels
+above half of D_max).
+
+Default workload: the batched configuration, 64 independent uneven plans
+(64^3 to 256^3 voxels of 0.2 to 0.5 cm, smoothed-noise densities of 0.2 to
+2.0 g/cm^3, 6 to 18 MeV photon or electron fields of 2 to 15 cm), each run
+from a zeroed tally to s_0.5 <= 1% (gpumcd_run_to_uncertainty: a first round
+of the plan's own history count, then rounds sized by s ~ 1/sqrt(N)).  One
+step = all 64 plans to 1%.
+- value: the batched form, every round of all active plans in one launch
+  sequence per particle type;
+- plain: the same plans one at a time with the same schedule (the same
+  histories and, bit for bit, the same tallies);
+- served: a Poisson stream of 1000 requests from the same distribution on
+  resident phantoms with continuous batching (serve.py), p50/p99 latency;
+- the paper's timing workload (1e6 e- + 4e6 photons, 15 MeV, 128^3 water) as a
+  sub-record.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload c4|c2|batched|served|geoms|ablation|kerma|grouping]
 
 Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs its own
 histories (weak scaling, no data-path collective); the time is the max over
@@ -26,11 +40,17 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "histories/s (1e6 e- + 4e6 photons, 15 MeV, 128^3 water, to FP64 dose + sigma)"
+METRIC = "histories/s at 1% dose uncertainty (plain vs batched/served); p50/p99 latency"
+METRIC_C2 = "histories/s (1e6 e- + 4e6 photons, 15 MeV, 128^3 water, to FP64 dose + sigma)"
 UNIT = "histories/s"
 N_E, N_G = 1_000_000, 4_000_000
-
-
+TARGET, THRESHOLD = 0.01, 0.5   # s_0.5 <= 1%
+W_C4 = 16                       # batch tallies per plan of the batched workload
+# ...and of the timing workload's beams: half the tally of 32 batches (268 MB
+# for 128^3), 3% faster transport (fewer L2 misses on the tally), with 15
+# degrees of freedom for sigma
+W_C2 = 16
+CAP_C4 = 400_000_000            # histories per plan at most
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -41,9 +61,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run each beam once at 1/5 of its histories (small case for ncu) and exit")
-    ap.add_argument("--workload", default="c2",
-                    choices=["c2", "batched", "served", "geoms", "ablation", "kerma", "grouping"],
-                    help="c2: the contract line; batched: 64 uneven plans in one launch vs alone; "
+    ap.add_argument("--workload", default="c4",
+                    choices=["c4", "c2", "batched", "served", "geoms", "ablation", "kerma", "grouping"],
+                    help="c4: the contract line (64 uneven plans to 1%%, batched vs plain vs served); "
+                         "c2: the paper's timing workload alone; "
+                         "batched: 64 uneven plans in one launch vs alone at fixed histories; "
                          "served: a Poisson request stream with continuous batching; geoms: the "
                          "paper's three geometries, each beam alone (Table resabsexec); ablation: "
                          "the lane refill policies on the second geometry (Table resdivred); "
@@ -61,6 +83,7 @@ def parse():
                     help="served: requests of the capacity run (served vs alone)")
     ap.add_argument("--target", type=float, default=0.01, help="served: relative uncertainty target")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="served: HBM budget")
+    ap.add_argument("--no-served", action="store_true", help="c4: leave out the served stream")
     return ap.parse_args()
 
 
@@ -125,32 +148,105 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def oracle_sample(seconds: float = 12.0, seed0: int = 100):
-    """Times the FP64 oracle (as it stands) on bounded samples of the workload
-    over all host cores: electrons and photons in the 1:4 ratio of the step.
-    Returns (histories/s, cores, description)."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def _oracle_job(job):
+    """Worker: the oracle, as it stands, on one sample (a workload's phantom and
+    beam, n histories).  An empty run of the same set-up is timed too and
+    subtracted, so the figure is the cost per history of a long run."""
     import oracle
     import workloads as W
 
-    cores = host_cores()
-    pe, pg = W.config2(W.ELECTRON), W.config2(W.PHOTON)
-    n_e, n_g = 150 * cores, 600 * cores
-    done = 0
+    kind, key, n, seed = job
+    if kind == "c4":
+        spec = W.config4()[key]
+        ph = spec.phantom()
+        src = W.square_field(spec.particle, spec.energy, ph, spec.field_cm)
+    else:
+        pl = W.config2(key)
+        ph, src = pl.phantom, pl.source
     t0 = time.perf_counter()
-    rounds = 0
-    while True:
-        oracle.simulate(W.MATERIALS, W.DEFAULT_PHYSICS, pe.phantom, pe.source, n_e, seed0 + rounds,
-                        processes=cores)
-        oracle.simulate(W.MATERIALS, W.DEFAULT_PHYSICS, pg.phantom, pg.source, n_g, seed0 + rounds,
-                        processes=cores)
-        done += n_e + n_g
-        rounds += 1
-        if time.perf_counter() - t0 > seconds:
-            break
-    dt = time.perf_counter() - t0
-    desc = (f"{rounds} round(s) of {n_e} e- + {n_g} photons (15 MeV, 10x10 cm^2, 128^3 water), "
-            f"{cores} processes")
-    return done / dt, cores, desc
+    oracle.simulate_range(W.MATERIALS, W.DEFAULT_PHYSICS, ph, src, 0, 0, seed)
+    t1 = time.perf_counter()
+    oracle.simulate_range(W.MATERIALS, W.DEFAULT_PHYSICS, ph, src, 0, n, seed)
+    t2 = time.perf_counter()
+    return kind, key, n, max((t2 - t1) - (t1 - t0), 1e-9)
+
+
+def oracle_rate(jobs, weights, cores: int):
+    """Runs the sample jobs over `cores` spawned processes at once.  Returns
+    (concurrent histories/s, one process's histories/s, histories timed, wall
+    s): the per-history cost of each job's workload is weighted by the
+    histories that workload holds in a step (weights[(kind, key)])."""
+    import multiprocessing as mp
+
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        out = pool.map(_oracle_job, jobs, chunksize=1)
+    wall = time.perf_counter() - t0
+    cost = {}
+    for kind, key, n, dt in out:
+        c = cost.setdefault((kind, key), [0, 0.0])
+        c[0] += n
+        c[1] += dt
+    tot_w = sum(weights[k] for k in cost)
+    per_hist = sum(weights[k] * c[1] / c[0] for k, c in cost.items()) / tot_w
+    one = 1.0 / per_hist
+    return one * cores, one, sum(c[0] for c in cost.values()), wall
+
+
+def c4_weights():
+    """Histories of each plan's first round in the batched workload (the
+    weights of the oracle's per-history costs)."""
+    import workloads as W
+    return {("c4", sp.index): -(-sp.n_histories // W_C4) * W_C4 for sp in W.config4()}
+
+
+def oracle_sample_c4(per_plan: int = 1500, seed0: int = 100):
+    """The FP64 oracle, as it stands, on a bounded sample of the batched
+    workload: every plan at `per_plan` histories, one process per plan, all
+    host cores at once; costs weighted by the plans' first-round histories."""
+    import workloads as W
+    cores = host_cores()
+    jobs = [("c4", sp.index, per_plan, seed0 + sp.index) for sp in W.config4()]
+    rate, one, n, wall = oracle_rate(jobs, c4_weights(), cores)
+    desc = (f"{per_plan} histories of each of the 64 plans ({n} in all, {wall:.1f} s wall), one process "
+            f"per plan over {cores} host cores, set-up excluded; per-history costs weighted by the plans' "
+            f"first-round histories")
+    return rate, one, cores, desc
+
+
+def oracle_sample_c2(seed0: int = 100):
+    """The oracle on a bounded sample of the paper's timing workload: 3000
+    electrons and 12000 photons per host core, in the 1:4 ratio of the step."""
+    import workloads as W
+    cores = host_cores()
+    jobs = []
+    for i in range(cores):
+        jobs.append(("c2", W.ELECTRON, 3000, seed0 + 2 * i))
+        jobs.append(("c2", W.PHOTON, 12000, seed0 + 2 * i + 1))
+    rate, one, n, wall = oracle_rate(jobs, {("c2", W.ELECTRON): N_E, ("c2", W.PHOTON): N_G}, cores)
+    desc = (f"{cores} x (3000 e- + 12000 photons), 15 MeV, 10x10 cm^2, 128^3 water ({n} histories, {wall:.1f} s "
+            f"wall) over {cores} host cores, set-up excluded")
+    return rate, one, cores, desc
 
 
 def rank_seed(rank: int, step: int) -> int:
@@ -173,29 +269,39 @@ def emit(obj):
 
 
 def run_reference(args):
+    """The oracle as it stands, timed on the host cores on bounded samples of
+    the workload (each step one sample); rank 0 only."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    for _ in range(args.warmup):
-        oracle_sample(seconds=3.0)
-    vals, descs, cores = [], None, host_cores()
-    t_all = 0.0
+    c2 = args.workload == "c2"
+    sample = oracle_sample_c2 if c2 else oracle_sample_c4
+    for i in range(args.warmup):
+        sample(seed0=10 * (i + 1)) if c2 else sample(per_plan=300, seed0=10 * (i + 1))
+    vals, ones, walls, desc, cores = [], [], [], None, host_cores()
     for i in range(args.steps):
-        v, cores, descs = oracle_sample(seconds=8.0, seed0=1000 + 10 * i)
+        t0 = time.perf_counter()
+        v, one, cores, desc = sample(seed0=1000 + 100 * i) if c2 else sample(per_plan=600, seed0=1000 + 100 * i)
+        walls.append(time.perf_counter() - t0)
         vals.append(v)
-        t_all += (N_E + N_G) / v
-    value = (N_E + N_G) * args.steps / t_all
-    emit({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
-          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-          "data": "synthetic",
-          "config": {"workload": "c2_water128_15MeV_e1e6_photon4e6", "parallelism": "host cores"},
-          "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                           "sample": descs},
+        ones.append(one)
+    value = statistics.mean(vals)
+    emit({"impl": "reference", "metric": METRIC_C2 if c2 else METRIC, "value": value, "unit": UNIT,
+          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+          "ms_per_step": 1e3 * statistics.mean(walls), "higher_is_better": True, "scaling": "weak",
+          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+          "config": {"workload": "c2_water128_15MeV_e1e6_photon4e6" if c2 else "c4_64_plans_to_1pct",
+                     "parallelism": "host cores",
+                     "step": "one bounded sample of the workload (below); the rate is per history, so "
+                             "it holds for any history count"},
+          "extrapolated": False,
+          "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+                           "single_core_value": statistics.mean(ones), "cpu_model": cpu_model()},
           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
 
 
-def run_ours(args):
+def run_c2(args):
+    """The paper's timing workload alone (its own JSON line)."""
     import torch
 
     import paper_1101_1245_gb300 as g
@@ -211,7 +317,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample()  # spawned processes, before the GPU work starts
+        cpu = oracle_sample_c2()  # spawned processes, before the GPU work starts
 
     pe, pg = W.config2(W.ELECTRON), W.config2(W.PHOTON)
     nvox = pe.phantom.nvox
@@ -221,8 +327,8 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     sh = stream.cuda_stream
     pid = ctx.create_phantom(pe.phantom)
-    plan_e = ctx.plan_open(pid, pe.source, 1, 32)
-    plan_g = ctx.plan_open(pid, pg.source, 2, 32)
+    plan_e = ctx.plan_open(pid, pe.source, 1, W_C2)
+    plan_g = ctx.plan_open(pid, pg.source, 2, W_C2)
     out = {k: torch.empty(nvox, dtype=torch.float64, device=dev) for k in ("de", "se", "dg", "sg")}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 2x the 129 MB L2
 
@@ -298,7 +404,7 @@ def run_ours(args):
     roof = rl.alu_roofline(ev_e, ev_g, kern_ms, clocks.get("sm_mhz"),
                            torch.cuda.get_device_properties(dev).multi_processor_count,
                            launches=st_e["n_launches"] + st_g["n_launches"])
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    line = {"metric": METRIC_C2, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "c2_water128_15MeV_e1e6_photon4e6",
@@ -317,8 +423,272 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clocks}
     if cpu:
-        line["cpu_baseline"] = {"value": cpu[0], "unit": UNIT, "cores": cpu[1], "kind": "oracle",
-                                "sample": cpu[2]}
+        line["cpu_baseline"] = {"value": cpu[0], "unit": UNIT, "cores": cpu[2], "kind": "oracle",
+                                "sample": cpu[3], "single_core_value": cpu[1], "cpu_model": cpu_model()}
+    if rank == 0:
+        emit(line)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def c4_seed(spec, rank: int, step: int) -> int:
+    """Seed of one plan of the batched workload in a step: every rank and step
+    simulates its own, disjoint histories."""
+    return (spec.seed + 1_000_003 * (rank + 1) + 7919 * (step + 1000)) % (1 << 62)
+
+
+def c2_subrecord(ctx, stream, steps: int, warmup: int, rank: int) -> dict:
+    """The paper's timing workload (1e6 e- + 4e6 photons at 15 MeV, 128^3
+    water at 0.25 cm), each beam from a zeroed tally to FP64 dose and sigma."""
+    import torch
+
+    import workloads as W
+    pe, pg = W.config2(W.ELECTRON), W.config2(W.PHOTON)
+    sh = stream.cuda_stream
+    pid = ctx.create_phantom(pe.phantom)
+    plan_e = ctx.plan_open(pid, pe.source, 1, W_C2)
+    plan_g = ctx.plan_open(pid, pg.source, 2, W_C2)
+    d = torch.empty(pe.phantom.nvox, dtype=torch.float64, device="cuda")
+    sg = torch.empty_like(d)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(i):
+        se = rank_seed(rank, i)
+        ctx.plan_reset(plan_e, se, sh)
+        ctx.run([plan_e], [N_E], sh)
+        a = ctx.plan_result(plan_e, THRESHOLD, d.data_ptr(), sg.data_ptr(), sh)
+        ctx.plan_reset(plan_g, se + 1, sh)
+        ctx.run([plan_g], [N_G], sh)
+        b = ctx.plan_result(plan_g, THRESHOLD, d.data_ptr(), sg.data_ptr(), sh)
+        return a, b
+
+    for i in range(warmup):
+        step(-1 - i)
+    ms, last = [], None
+    for i in range(steps):
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            ev[0].record(stream)
+            last = step(i)
+            ev[1].record(stream)
+        torch.cuda.synchronize()
+        ms.append(ev[0].elapsed_time(ev[1]))
+    ctx.plan_close(plan_e)
+    ctx.plan_close(plan_g)
+    ctx.destroy_phantom(pid)
+    a, b = last
+    return {"workload": "c2_water128_15MeV_e1e6_photon4e6", "metric": METRIC_C2,
+            "value": (N_E + N_G) / (statistics.median(ms) / 1e3), "ms_per_step": statistics.median(ms),
+            "steps": steps, "transport_ms_electron": a["transport_ms"], "transport_ms_photon": b["transport_ms"],
+            "s05_electron": a["s_thr"], "s05_photon": b["s_thr"],
+            "events_electron_beam": a["n_electron_steps"] + a["n_photon_events"],
+            "events_photon_beam": b["n_electron_steps"] + b["n_photon_events"],
+            "ledger_exact": all(x["e_deposited"] + x["e_escaped"] + x["e_rest"] == x["e_incident"] for x in last)}
+
+
+def run_c4(args):
+    """The contract line: the batched workload's 64 plans, each to s_0.5 <= 1%."""
+    import numpy as np
+    import torch
+
+    import paper_1101_1245_gb300 as g
+    import paper_1101_1245_gb300.roofline as rl
+    import workloads as W
+    from paper_1101_1245_gb300.autotune import autotune
+
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample_c4()  # spawned processes, before the GPU work starts
+
+    def log(msg):
+        if rank == 0:
+            print(f"[bench] {msg}", file=sys.stderr, flush=True)
+
+    specs = W.config4()
+    phantoms = c4_phantoms(specs)
+    log("phantoms ready")
+    ctx = g.engine(local)
+    if args.graph:
+        ctx.set_launch(flags=g.LAUNCH_GRAPH)
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+    pids = [ctx.create_phantom(ph) for ph in phantoms]
+    srcs = [W.square_field(sp.particle, sp.energy, ph, sp.field_cm) for sp, ph in zip(specs, phantoms)]
+    first = [-(-sp.n_histories // W_C4) * W_C4 for sp in specs]
+    caps = [CAP_C4] * len(specs)
+    # the launch, tuned on the whole plan set at 1/8 of its first round in one launch
+    sample = [(pids[i], srcs[i], max(W_C4, first[i] // 8 // W_C4 * W_C4)) for i in range(len(specs))]
+    tuned = autotune(ctx, sample, reps=2)
+    log(f"autotuned: {tuned['launch']}")
+    plans = [ctx.plan_open(pid, src, sp.seed, W_C4) for pid, src, sp in zip(pids, srcs, specs)]
+
+    def seeds(step):
+        return [c4_seed(sp, rank, step) for sp in specs]
+
+    def batched(step):
+        for p, sd in zip(plans, seeds(step)):
+            ctx.plan_reset(p, sd, sh)
+        return ctx.run_to_uncertainty(plans, first, caps, TARGET, THRESHOLD, sh)
+
+    def plain(step):
+        out = {"histories": [], "s_thr": [], "rounds": 0, "transport_ms": 0.0}
+        for p, sd, f, c in zip(plans, seeds(step), first, caps):
+            ctx.plan_reset(p, sd, sh)
+            r = ctx.run_to_uncertainty([p], [f], [c], TARGET, THRESHOLD, sh)
+            out["histories"] += r["histories"]
+            out["s_thr"] += r["s_thr"]
+            out["rounds"] += r["rounds"]
+            out["transport_ms"] += r["transport_ms"]
+        return out
+
+    def timed(fn, step):
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            r = fn(step)
+            ev[1].record(stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]), r
+
+    for i in range(args.warmup):
+        batched(-1 - i)
+    log("warm")
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    res = []
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            res.append(timed(batched, i))
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_ms = max_over_ranks(sum(r[0] for r in res), dist, dev)
+    hist_steps = [sum(r[1]["histories"]) for r in res]
+    value = sum(hist_steps) * world / (total_ms / 1e3)
+    clocks = clk.summary()
+    log(f"batched {value:.3e} histories/s, {total_ms / args.steps:.0f} ms per step")
+
+    # counters of the last timed step: a sequence's event counts go to its first
+    # plan, so summing over each type's plans gives that type's sequences
+    st = [ctx.plan_result(p, THRESHOLD) for p in plans]
+    ev_type = {t: sum(x["n_electron_steps"] + x["n_photon_events"] for x, sp in zip(st, specs) if sp.particle == t)
+               for t in (W.ELECTRON, W.PHOTON)}
+    last = res[-1][1]
+    ledger_ok = all(x["e_deposited"] + x["e_escaped"] + x["e_rest"] == x["e_incident"] for x in st)
+    # per plan, n_launches counts the launches of the sequences it ran in (its
+    # rounds, one launch each unless a queue overflowed): the folds; a round
+    # runs one sequence per particle type
+    folds = sum(x["n_launches"] for x in st)
+    transport_launches = sum(max((x["n_launches"] for x, sp in zip(st, specs) if sp.particle == t), default=0)
+                             for t in (W.ELECTRON, W.PHOTON))
+    launches = transport_launches + 2 * folds  # + the fold and s_thr kernels of every fold
+
+    # the plain form: the same plans one at a time, same seeds and schedule
+    plain_runs = [timed(plain, i) for i in range(min(2, args.steps))]
+    same = all(p[1]["histories"] == res[i][1]["histories"] and p[1]["s_thr"] == res[i][1]["s_thr"]
+               for i, p in enumerate(plain_runs))
+    plain_value = sum(sum(p[1]["histories"]) for p in plain_runs) / (sum(p[0] for p in plain_runs) / 1e3)
+    batched_ms = statistics.median(r[0] for r in res[:len(plain_runs)])
+    log(f"plain {plain_value:.3e} histories/s")
+
+    # the paper's timing workload, as a sub-record
+    for p in plans:
+        ctx.plan_close(p)
+    c2 = c2_subrecord(ctx, stream, steps=5, warmup=2, rank=rank) if rank == 0 else None
+
+    # end to end through the C ABI with host buffers: each step uploads the 64
+    # phantoms from pinned host memory, runs them to 1% and reads dose and
+    # sigma back into pinned host memory
+    def pinned(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+    ph_host = [W.Phantom(ph.dims, ph.voxel_cm, pinned(ph.mat), pinned(ph.rho)) for ph in phantoms]
+    out_d = [torch.empty(ph.nvox, dtype=torch.float64, pin_memory=True).numpy() for ph in phantoms]
+    out_s = [torch.empty(ph.nvox, dtype=torch.float64, pin_memory=True).numpy() for ph in phantoms]
+
+    def e2e_step(step):
+        pid2 = [ctx.create_phantom(ph) for ph in ph_host]
+        pl2 = [ctx.plan_open(pid, src, sd, W_C4) for pid, src, sd in zip(pid2, srcs, seeds(step))]
+        r = ctx.run_to_uncertainty(pl2, first, caps, TARGET, THRESHOLD)
+        for p, d, s_ in zip(pl2, out_d, out_s):
+            ctx.plan_result_host(p, THRESHOLD, d, s_)
+        for p in pl2:
+            ctx.plan_close(p)
+        for pid in pid2:
+            ctx.destroy_phantom(pid)
+        return sum(r["histories"])
+
+    e2e_step(0)  # warm-up (fills the device-memory cache)
+    e2e = []
+    for i in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = e2e_step(i + 1)
+        e2e.append(h / (time.perf_counter() - t0))
+    e2e_val = statistics.median(e2e) * world
+    h2d = sum(ph.mat.nbytes + ph.rho.nbytes for ph in phantoms)
+    d2h = sum(16 * ph.nvox for ph in phantoms)
+    log(f"e2e {e2e_val:.3e} histories/s")
+
+    served = served_leg(ctx, phantoms, pids, args) if rank == 0 and not args.no_served else None
+    if served:
+        log(f"served stream {served['stream_value']:.3e} histories/s, p50 {served['latency_p50_s']:.2f} s, "
+            f"p99 {served['latency_p99_s']:.2f} s")
+
+    roof = rl.alu_roofline_c4(ev_type[W.ELECTRON], ev_type[W.PHOTON], last["transport_ms"],
+                              clocks.get("sm_mhz"), torch.cuda.get_device_properties(dev).multi_processor_count,
+                              launches=transport_launches)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "c4_64_plans_to_1pct",
+                       "plans": "64 uneven plans (config 4, seed 4): 64^3-256^3 voxels of 0.2-0.5 cm, "
+                                "smoothed-noise densities 0.2-2.0 g/cm^3, 6-18 MeV photon or electron fields "
+                                "of 2-15 cm",
+                       "target": f"s_0.5 <= {TARGET:g} per plan (mean sigma/D over voxels above 0.5 D_max)",
+                       "schedule": "first round = the plan's own history count, then rounds sized by "
+                                   "s ~ 1/sqrt(N) (gpumcd_run_to_uncertainty); at most 4e8 histories a plan",
+                       "form": "batched: each round of all active plans in one launch sequence per particle "
+                               "type (autotuned launch)",
+                       "histories_per_step": statistics.median(hist_steps),
+                       "rounds_per_step": last["rounds"],
+                       "transport_ms_per_step": last["transport_ms"],
+                       "plans_at_cap": sum(1 for h in last["histories"] if h >= CAP_C4),
+                       "s_thr_max": max(last["s_thr"]),
+                       "n_batches": W_C4,
+                       "l2": "inputs larger than L2: 52 GB of batch tallies per step",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "launch": tuned["launch"], "launch_graph": bool(args.graph),
+                       "ledger_exact": ledger_ok},
+            "plain": {"value": plain_value, "passes": len(plain_runs),
+                      "ms_per_step": statistics.median(p[0] for p in plain_runs),
+                      "batched_ms_same_seeds": batched_ms,
+                      "batched_over_plain": statistics.median(p[0] for p in plain_runs) / batched_ms,
+                      "same_histories_and_s_as_batched": same,
+                      "form": "each plan alone, the same seeds and schedule (gpumcd_run_to_uncertainty "
+                              "with one plan)"},
+            "served": served,
+            "c2": c2,
+            "roofline": roof,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "host_memory": "pinned", "steps": len(e2e),
+                    "form": "64 phantoms uploaded, run to 1% batched, dose and sigma read back, per step"},
+            "gpu_launches": launches,
+            "clocks": clocks}
+    if cpu:
+        line["cpu_baseline"] = {"value": cpu[0], "unit": UNIT, "cores": cpu[2], "kind": "oracle",
+                                "sample": cpu[3], "single_core_value": cpu[1], "cpu_model": cpu_model()}
     if rank == 0:
         emit(line)
     ctx.close()
@@ -700,24 +1070,17 @@ def run_grouping(args):
           "phantom": "128^3 water at 0.25 cm", "data": "synthetic", "rows": rows})
 
 
-def run_served(args):
+def served_leg(ctx, phantoms, pids, args) -> dict:
     """Config 5: a Poisson stream of dose requests from the config-4
-    distribution on resident phantoms, served with continuous batching to a
-    relative uncertainty target over voxels above 50% of D_max; against the
-    same requests run one by one."""
-    import numpy as np
-
-    import paper_1101_1245_gb300 as g
+    distribution on resident phantoms (request i on phantom i mod 64), served
+    with continuous batching to s_0.5 <= target; first a capacity run of a
+    calibration set all present at once, against the same requests run one by
+    one with the plain schedule (serve.run_alone), then the stream at 0.8 x that
+    capacity."""
     import workloads as W
     from paper_1101_1245_gb300.serve import DoseRequest, Server, run_alone
 
-    pool_specs = W.config4()
-    phantoms = c4_phantoms(pool_specs)
     budget = int(args.budget_gb * 2 ** 30)
-    ctx = g.engine(0, hbm_budget_bytes=budget + (8 << 30))
-    if args.graph:
-        ctx.set_launch(flags=g.LAUNCH_GRAPH)
-    pids = [ctx.create_phantom(ph) for ph in phantoms]
 
     def requests(rate):
         reqs = []
@@ -725,11 +1088,9 @@ def run_served(args):
             k = i % len(phantoms)
             ph, sp = phantoms[k], r.spec
             src = W.square_field(sp.particle, sp.energy, ph, sp.field_cm)
-            reqs.append(DoseRequest(i, pids[k], ph.nvox, src, sp.seed, r.arrival_s, 400_000_000))
+            reqs.append(DoseRequest(i, pids[k], ph.nvox, src, sp.seed, r.arrival_s, CAP_C4))
         return reqs
 
-    # capacity: a calibration set all present at once, served, against the
-    # same requests run one at a time with the plain kernel
     cal = requests(1.0)[:min(args.calibration, args.requests)]
     srv = Server(ctx, budget, target=args.target, round_histories=args.round_histories,
                  rounds_in_flight=args.rounds_in_flight)
@@ -742,44 +1103,80 @@ def run_served(args):
     alone_t = sum(a.done_s for a in alone)
     mean_h = rep_cal["histories"] / max(rep_cal["requests"], 1)
     rate = 0.8 * rep_cal["histories_per_s"] / mean_h
-    # the stream: Poisson arrivals at 0.8 x that capacity
     srv = Server(ctx, budget, target=args.target, round_histories=args.round_histories,
                  rounds_in_flight=args.rounds_in_flight)
-    reqs = requests(rate)
-    for q in reqs:
+    for q in requests(rate):
         srv.submit(q)
     srv.run(real_time=True)
     rep = srv.report()
+    return {"target": args.target, "threshold": THRESHOLD,
+            "capacity_value": rep_cal["histories_per_s"],
+            "alone_value": alone_h / alone_t if alone_t else None,
+            "served_over_alone": rep_cal["histories_per_s"] * alone_t / alone_h if alone_h else None,
+            "capacity_requests": len(cal), "capacity_histories": rep_cal["histories"],
+            "alone_histories": alone_h, "capacity_rounds": rep_cal["rounds"],
+            "requests": rep["requests"], "arrival_rate_per_s": rate,
+            "rate_basis": "0.8 x the served capacity on the calibration set",
+            "stream_value": rep["histories_per_s"], "latency_p50_s": rep["latency_p50_s"],
+            "latency_p99_s": rep["latency_p99_s"], "wall_s": rep["wall_s"], "rounds": rep["rounds"],
+            "folds": rep["folds"], "mean_histories_per_request": rep["histories"] / max(rep["requests"], 1),
+            "s_thr_max": rep["s_thr_max"], "rounds_in_flight": args.rounds_in_flight,
+            "round_histories": args.round_histories, "hbm_budget_gb": args.budget_gb,
+            "max_histories_per_request": CAP_C4,
+            "phantoms": "64 resident config-4 phantoms, request i on phantom i mod 64"}
+
+
+def run_served(args):
+    import paper_1101_1245_gb300 as g
+    import workloads as W
+
+    phantoms = c4_phantoms(W.config4())
+    ctx = g.engine(0, hbm_budget_bytes=int(args.budget_gb * 2 ** 30) + (8 << 30))
+    if args.graph:
+        ctx.set_launch(flags=g.LAUNCH_GRAPH)
+    pids = [ctx.create_phantom(ph) for ph in phantoms]
+    out = served_leg(ctx, phantoms, pids, args)
     emit({"workload": "c5_served", "metric": "histories/s and request latency at s_0.5 <= target",
-          "unit": UNIT, "target": args.target, "threshold": 0.5,
-          "served_capacity_value": rep_cal["histories_per_s"],
-          "alone_value": alone_h / alone_t if alone_t else None,
-          "served_over_alone": rep_cal["histories_per_s"] * alone_t / alone_h if alone_h else None,
-          "capacity_requests": len(cal), "capacity_histories": rep_cal["histories"],
-          "alone_histories": alone_h, "capacity_rounds": rep_cal["rounds"],
-          "requests": rep["requests"], "arrival_rate_per_s": rate,
-          "rate_basis": "0.8 x the served capacity on the calibration set",
-          "stream_value": rep["histories_per_s"], "latency_p50_s": rep["latency_p50_s"],
-          "latency_p99_s": rep["latency_p99_s"], "wall_s": rep["wall_s"], "rounds": rep["rounds"],
-          "folds": rep["folds"], "mean_histories_per_request": rep["histories"] / max(rep["requests"], 1),
-          "s_thr_max": rep["s_thr_max"], "rounds_in_flight": args.rounds_in_flight,
-          "round_histories": args.round_histories, "hbm_budget_gb": args.budget_gb,
-          "launch_graph": bool(args.graph),
-          "phantoms": "64 resident config-4 phantoms, request i on phantom i mod 64", "data": "synthetic"})
+          "unit": UNIT, **out, "launch_graph": bool(args.graph), "data": "synthetic"})
     ctx.close()
 
 
-def run_ncu_case():
-    """Each beam of the step once at 1/5 of its histories, untimed: the small
-    case profiled with ncu --set full (one launch of the transport kernel per beam)."""
+def run_ncu_case(args):
+    """A small case of the workload for ncu, untimed.  c2: each beam once at 1/5
+    of its histories (one transport launch per beam).  c4: the batched
+    workload's plans of at most 160^3 voxels (8 batch tallies each, a few GB on
+    the device), one round at 1/10 of their first-round histories: one
+    transport launch per particle type.  Prints each launch's event counts."""
     import paper_1101_1245_gb300 as g
     import workloads as W
 
     ctx = g.engine(0)
+    if args.workload == "c4":
+        specs = [sp for sp in W.config4() if sp.n <= 160]
+        phantoms = c4_phantoms(specs)
+        pids = [ctx.create_phantom(ph) for ph in phantoms]
+        for t in (W.ELECTRON, W.PHOTON):
+            idx = [i for i, sp in enumerate(specs) if sp.particle == t]
+            plans = [ctx.plan_open(pids[i], W.square_field(specs[i].particle, specs[i].energy, phantoms[i],
+                                                           specs[i].field_cm), specs[i].seed, 8) for i in idx]
+            n = [max(8, specs[i].n_histories // 10 // 8 * 8) for i in idx]
+            ctx.run(plans, n)
+            st = [ctx.plan_result(p, 0.5) for p in plans]
+            print(json.dumps({"case": "c4_small_" + ("electron" if t == W.ELECTRON else "photon"),
+                              "plans": len(plans), "histories": sum(n),
+                              "voxels": int(sum(phantoms[i].nvox for i in idx)),
+                              **{k: sum(x[k] for x in st) for k in (
+                                  "n_electron_steps", "n_photon_events", "n_hard_real")},
+                              "n_launches": st[0]["n_launches"], "transport_ms": st[0]["transport_ms"]}),
+                  flush=True)
+            for p in plans:
+                ctx.plan_close(p)
+        ctx.close()
+        return
     for part, n in ((W.ELECTRON, N_E // 5), (W.PHOTON, N_G // 5)):
         pl = W.config2(part)
         pid = ctx.create_phantom(pl.phantom)
-        plan = ctx.plan_open(pid, pl.source, 5, 32)
+        plan = ctx.plan_open(pid, pl.source, 5, W_C2)
         ctx.run([plan], [n])
         st = ctx.plan_result(plan, 0.5)
         print(json.dumps({"case": pl.name, "histories": n, **{k: st[k] for k in (
@@ -793,30 +1190,14 @@ def run_ncu_case():
 def main():
     args = parse()
     if args.ncu_case:
-        run_ncu_case()
-        return
-    if args.workload == "batched":
-        run_batched(args)
-        return
-    if args.workload == "served":
-        run_served(args)
-        return
-    if args.workload == "geoms":
-        run_geoms(args)
-        return
-    if args.workload == "ablation":
-        run_ablation(args)
-        return
-    if args.workload == "kerma":
-        run_kerma(args)
-        return
-    if args.workload == "grouping":
-        run_grouping(args)
+        run_ncu_case(args)
         return
     if args.impl == "reference":
         run_reference(args)
-    else:
-        run_ours(args)
+        return
+    run = {"c4": run_c4, "c2": run_c2, "batched": run_batched, "served": run_served, "geoms": run_geoms,
+           "ablation": run_ablation, "kerma": run_kerma, "grouping": run_grouping}
+    run[args.workload](args)
 
 
 if __name__ == "__main__":

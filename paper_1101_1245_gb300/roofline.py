@@ -25,10 +25,10 @@ from typing import Optional
 # these are the algorithmic figures
 INST_PER_EVENT_E_BEAM: Optional[float] = 19.68
 INST_PER_EVENT_PH_BEAM: Optional[float] = 18.81
-# DRAM bytes (read + write) per transport launch of the benchmark step, from ncu on
-# the same workload at 1/5 of its histories, scaled by histories (790 MB electron
-# launch, 4.95 GB photon launch); None once the kernel has changed since the capture
-TRAFFIC_BYTES_PER_LAUNCH: Optional[float] = 2.87e9
+# DRAM bytes (read + write) per transport launch of the timing workload: measured with
+# 32 batch tallies (2.87e9 per launch); the benchmark now runs it with 16, whose tally
+# traffic that capture does not describe, so None until it is captured again
+TRAFFIC_BYTES_PER_LAUNCH: Optional[float] = None
 
 
 def alu_roofline(events_e_beam: int, events_ph_beam: int, kernel_ms: float, sm_mhz: Optional[float],
@@ -43,6 +43,46 @@ def alu_roofline(events_e_beam: int, events_ph_beam: int, kernel_ms: float, sm_m
         work = events_e_beam * INST_PER_EVENT_E_BEAM + events_ph_beam * INST_PER_EVENT_PH_BEAM
         out["achieved"] = work / (kernel_ms / 1e3) / 1e9
         out["work_warp_inst_per_launch"] = work / max(launches, 1)
+        if peak:
+            out["frac"] = out["achieved"] / peak
+    return out
+
+
+# The same figures for the batched workload (64 uneven plans of smoothed-noise
+# densities, 6-18 MeV photon or electron fields): converged warp-instructions
+# per transport event (smsp__thread_inst_executed.sum / 32 / events) in the
+# electron-beam and the photon-beam launch sequences, from ncu on the
+# workload's 27 plans of at most 160^3 voxels at 1/10 of their first round
+# (bench.py --ncu-case --workload c4): 144.79e9 thread-instructions over
+# 259.66e6 events, and 72.61e9 over 128.58e6.  Kept fixed as the algorithmic
+# work per event, so a faster kernel shows as a higher achieved rate.
+INST_PER_EVENT_C4_E_SEQ: Optional[float] = 17.43
+INST_PER_EVENT_C4_PH_SEQ: Optional[float] = 17.65
+# DRAM bytes (read + write) per event of that capture: 2.018 GB over 259.66e6
+# events (electron sequence) and 1.953 GB over 128.58e6 (photon sequence)
+TRAFFIC_BYTES_PER_EVENT_C4_E_SEQ: Optional[float] = 7.77
+TRAFFIC_BYTES_PER_EVENT_C4_PH_SEQ: Optional[float] = 15.19
+
+
+def alu_roofline_c4(events_e_seq: int, events_ph_seq: int, kernel_ms: float, sm_mhz: Optional[float],
+                    n_sm: int, launches: int) -> dict:
+    """SM-issue roofline of the transport launches of one step of the batched
+    workload: events of the electron-beam and photon-beam sequences, the device
+    time of all `launches` of them; work and traffic per average launch."""
+    peak = n_sm * 4 * sm_mhz * 1e6 / 1e9 if sm_mhz else None
+    n = max(launches, 1)
+    out = {"bound": "alu", "unit": "Gwarp-inst/s", "peak": peak, "achieved": None, "frac": None,
+           "traffic": None, "peak_basis": f"{n_sm} SMs x 4 warp-inst/clk x median sampled SM clock",
+           "events_per_step": events_e_seq + events_ph_seq, "launches_per_step": launches}
+    if TRAFFIC_BYTES_PER_EVENT_C4_E_SEQ is not None and TRAFFIC_BYTES_PER_EVENT_C4_PH_SEQ is not None:
+        out["traffic"] = (TRAFFIC_BYTES_PER_EVENT_C4_E_SEQ * events_e_seq
+                          + TRAFFIC_BYTES_PER_EVENT_C4_PH_SEQ * events_ph_seq) / n
+        out["traffic_basis"] = ("DRAM bytes per average transport launch: ncu bytes per event of the small case "
+                                "(electron / photon sequences) x the step's events / its launches")
+    if INST_PER_EVENT_C4_E_SEQ is not None and INST_PER_EVENT_C4_PH_SEQ is not None and kernel_ms > 0:
+        work = events_e_seq * INST_PER_EVENT_C4_E_SEQ + events_ph_seq * INST_PER_EVENT_C4_PH_SEQ
+        out["achieved"] = work / (kernel_ms / 1e3) / 1e9
+        out["work_warp_inst_per_launch"] = work / n
         if peak:
             out["frac"] = out["achieved"] / peak
     return out

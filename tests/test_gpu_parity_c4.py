@@ -5,20 +5,21 @@ electron fields of 2 to 15 cm) against the FP64 oracle on the same seeded
 phantoms and beams.
 
 All 64 plans run in one batched launch sequence per particle type (16 batches
-each, as the benchmark runs them); the oracle runs each plan at 5e4
-histories in K = 8 independent parts, the GPU at 100 times that, so the
+each, as the benchmark runs them); the oracle runs each plan at 2e5
+histories in K = 8 independent parts, the GPU at 50 times that, so the
 comparison's noise is the oracle's.  The compared voxels come from a third,
 independent GPU run (other seeds): choosing them by either compared side's
 own noisy dose would favour its upward fluctuations (regression to the mean).
 
-At 5e4 histories the oracle sees few events in most voxels of a photon plan,
-where its per-voxel sigma is degenerate (an oracle run against a second
-oracle run fails a per-voxel 3-sigma test there just as often), so:
+At these counts the oracle sees few events in most voxels of a photon plan,
+where its per-voxel sigma is degenerate and skewed (an oracle run against a
+second oracle run fails a per-voxel 3-sigma test there just as often: 89-91%
+of the voxels pass on two photon plans), so:
 - per voxel, where the oracle's expected relative sigma (from the independent
-  run) is under 30%: >= 97% of a plan's voxels (plans with >= 30 such voxels)
-  and >= 99% of all of them within 3 combined sigma; where it is under 10%,
-  z-scores of mean ~0 and spread ~1, which also checks both uncertainty
-  estimators;
+  run) is under 10% (a hundred or more events): >= 97% of a plan's voxels
+  (plans with >= 30 such voxels) and >= 99% of all of them within 3 combined
+  sigma, and z-scores of mean ~0 and spread ~1, which also checks both
+  uncertainty estimators;
 - per block of 4 x 4 x 4 voxels above 10% of the block D_max, for every plan:
   the GPU's mass-weighted block dose against the mean of the oracle's K parts
   with the standard error of their spread (a t statistic with K - 1 degrees of
@@ -41,8 +42,8 @@ from tests.gpu_common import ledger_exact, make_ctx
 
 pytestmark = pytest.mark.gpu
 
-N_ORACLE = 50_000
-N_GPU = 100 * N_ORACLE
+N_ORACLE = 200_000
+N_GPU = 50 * N_ORACLE
 K = 8      # independent oracle parts
 B = 4      # block edge in voxels
 
@@ -97,7 +98,7 @@ def test_batched_workload_plans_against_oracle():
             sp = specs[len(plans)]
             src = W.square_field(sp.particle, sp.energy, ph, sp.field_cm)
             plans.append(ctx.plan_open(pid, src, sp.seed, 16))
-            sel.append(ctx.plan_open(pid, src, sp.seed + 1, 8))
+            sel.append(ctx.plan_open(pid, src, sp.seed + 1, 16))
             rhos.append(np.ascontiguousarray(ph.rho, dtype=np.float32).ravel())
             vol.append(float(np.prod(ph.voxel_cm)))
         ctx.run(plans, [N_GPU] * len(plans))
@@ -118,10 +119,10 @@ def test_batched_workload_plans_against_oracle():
             # from the independent run scaled to the oracle's history count)
             with np.errstate(divide="ignore", invalid="ignore"):
                 rel_o = np.where(ds > 0, ss / ds, np.inf) * np.sqrt(N_GPU / N_ORACLE)
-            dense = (ds > 0.1 * ds.max()) & (rel_o < 0.3)
+            dense = (ds > 0.1 * ds.max()) & (rel_o < 0.1)
             z = (dg - do)[dense] / np.sqrt(sg ** 2 + so ** 2)[dense]
             rates[idx] = (float(np.mean(np.abs(z) <= 3.0)) if z.size else 1.0, int(dense.sum()))
-            zs.append(z[rel_o[dense] < 0.1])
+            zs.append(z)
             # per block of B^3 voxels: mass-weighted doses, Gy per history
             mb = _blocks(rho, n)
             with np.errstate(divide="ignore", invalid="ignore"):
@@ -147,7 +148,7 @@ def test_batched_workload_plans_against_oracle():
     bad = {i: r for i, r in rates.items() if r[1] >= 30 and r[0] < 0.97}
     assert not bad, bad
     n_dense = sum(r[1] for r in rates.values())
-    assert n_dense > 10_000, n_dense
+    assert n_dense > 2_000, n_dense
     pooled = sum(r[0] * r[1] for r in rates.values()) / n_dense
     assert pooled >= 0.99, pooled
     bad = {i: r for i, r in brates.items() if r[1] >= 50 and r[0] < 0.97}
@@ -156,9 +157,8 @@ def test_batched_workload_plans_against_oracle():
     bpooled = sum(r[0] * r[1] for r in brates.values()) / sum(r[1] for r in brates.values())
     assert bpooled >= 0.985, bpooled
     z = np.concatenate(zs)
-    if z.size >= 2000:
-        assert abs(float(np.mean(z))) < 0.1, (float(np.mean(z)), float(np.std(z)), z.size)
-        assert 0.85 < float(np.std(z)) < 1.15, (float(np.mean(z)), float(np.std(z)), z.size)
+    assert abs(float(np.mean(z))) < 0.1, (float(np.mean(z)), float(np.std(z)), z.size)
+    assert 0.85 < float(np.std(z)) < 1.15, (float(np.mean(z)), float(np.std(z)), z.size)
     for t in (0, 1):
         n_plans = sum(1 for sp in specs if sp.particle == t)
         for k, (g_count, o_count) in counts[t].items():
