@@ -121,10 +121,10 @@ typedef struct {
      * of 7 doubles, x, y, z (cm), ux, uy, uz (normalised on upload), E (MeV,
      * in (0, e_max]), all of `particle`; history h starts as record h mod n.
      * Host array, copied at gpumcd_plan_open; energy and spectrum are ignored.
-     * A launch holding such a plan runs a separately compiled kernel
-     * (blocks_per_sm <= 2, none of the GPUMCD_LAUNCH_PROFILE,
-     * GPUMCD_LAUNCH_WARP_AGGREGATE, GPUMCD_LAUNCH_KERMA flags nor a
-     * refill_period other than 1: else GPUMCD_ERR_INVALID_ARG at run time). */
+     * A launch holding such a plan runs a separately compiled kernel (none of
+     * the GPUMCD_LAUNCH_PROFILE, GPUMCD_LAUNCH_WARP_AGGREGATE,
+     * GPUMCD_LAUNCH_KERMA flags nor a refill_period other than 1: else
+     * GPUMCD_ERR_INVALID_ARG at run time). */
     int32_t n_phase_space;
     const double *phase_space;
     /* GPUMCD_ENERGY_UNGROUPED or GPUMCD_ENERGY_GROUPED (another value:
@@ -154,22 +154,21 @@ typedef struct {
  * considers a low-occupancy type switch only on refill passes.  Hard-event
  * passes and type switches by stack level stay on in every form.  The
  * tallies do not depend on the form.  A form other than 1 runs a separately
- * compiled kernel: it needs blocks_per_sm <= 2 and none of GPUMCD_LAUNCH_PROFILE,
+ * compiled kernel: it needs none of GPUMCD_LAUNCH_PROFILE,
  * GPUMCD_LAUNCH_WARP_AGGREGATE or GPUMCD_LAUNCH_KERMA (else GPUMCD_ERR_INVALID_ARG). */
 #define GPUMCD_REFILL_WHEN_EMPTY 0xFFFFFFFFu
 
 #define GPUMCD_LAUNCH_WARP_AGGREGATE 1u /* combine a warp's deposits to one voxel into one atomic */
 #define GPUMCD_LAUNCH_PROFILE 2u        /* count clock cycles per event type (see gpumcd_debug_counters) */
-/* The two flags above select separately compiled kernels: each needs blocks_per_sm <= 2, and
- * they cannot be combined with each other, with GPUMCD_LAUNCH_KERMA or with a refill_period
- * other than 1 (GPUMCD_ERR_INVALID_ARG). */
+/* The two flags above select separately compiled kernels: they cannot be combined with each
+ * other, with GPUMCD_LAUNCH_KERMA or with a refill_period other than 1 (GPUMCD_ERR_INVALID_ARG). */
 #define GPUMCD_LAUNCH_GRAPH 4u          /* replay a sequence's first launch from a captured CUDA graph */
 /* Photon-only transport: every electron (a photon's secondary, or a primary) deposits its
  * kinetic energy in the voxel where it is created, and no electron is transported.  The
  * "photon-only fast mode" of the paper's outlook; the dose is then the kerma of the photon
  * field (kinetic energy released per mass), not the absorbed dose.  A separately compiled
- * kernel: it needs blocks_per_sm <= 2 and none of GPUMCD_LAUNCH_PROFILE,
- * GPUMCD_LAUNCH_WARP_AGGREGATE or a refill_period other than 1 (else GPUMCD_ERR_INVALID_ARG). */
+ * kernel: it needs none of GPUMCD_LAUNCH_PROFILE, GPUMCD_LAUNCH_WARP_AGGREGATE or a
+ * refill_period other than 1 (else GPUMCD_ERR_INVALID_ARG). */
 #define GPUMCD_LAUNCH_KERMA 8u
 
 /* Counters of one run.  The ledger satisfies, exactly,
@@ -377,10 +376,13 @@ gpumcd_status gpumcd_plan_result_noalloc(gpumcd_ctx *ctx, int32_t plan_id, doubl
 /* ---- launch tuning ------------------------------------------------------ */
 
 /* Sets the launch of later runs; fields left 0 keep their value.  A new
- * context starts at 512 threads x 2 CTAs per SM, stack_capacity 512,
+ * context starts at 1024 threads x 1 CTA per SM, stack_capacity 512,
  * switch_high 320, refill_low 16, chunk 32, overflow_capacity 2^20, flags 0.
- * Supported shapes are blocks_per_sm 1 or 2 with block_threads <= 512, and
- * blocks_per_sm 3 or 4 with block_threads <= 256.  Also required:
+ * Supported shapes have block_threads a multiple of 32, 1 <= blocks_per_sm
+ * <= 4 and at most 1024 threads per SM (block_threads x blocks_per_sm):
+ * shapes of up to 512 threads per SM run a kernel with 128 registers a
+ * thread, up to 768 (at most 384 a CTA) one with 80, the others one with 64.
+ * Also required:
  * 128 <= stack_capacity <= 65536, 32 <= switch_high <= stack_capacity,
  * refill_low <= 32, 1 <= chunk <= 4096 and 64 <= overflow_capacity <= 2^26.
  * Anything else returns GPUMCD_ERR_INVALID_ARG, and so does a call while a

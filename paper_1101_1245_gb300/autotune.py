@@ -18,8 +18,10 @@ from typing import Dict, List, Sequence, Tuple
 
 from . import ERR_INVALID_ARG, Context, GpumcdError
 
-# (block_threads, blocks_per_sm) shapes with a kernel variant behind them
-SHAPES: List[Tuple[int, int]] = [(512, 2), (384, 2), (256, 3), (256, 4), (512, 1)]
+# (block_threads, blocks_per_sm) shapes with a kernel variant behind them: 32
+# warps per SM in one CTA (64 registers, one copy of the tables per SM) or two,
+# 24 warps (80 registers), 16 warps (128 registers)
+SHAPES: List[Tuple[int, int]] = [(1024, 1), (512, 2), (384, 2), (256, 3), (512, 1)]
 KNOBS: Dict[str, List[int]] = {
     "chunk": [16, 32, 64],
     "switch_high": [200, 320, 384],

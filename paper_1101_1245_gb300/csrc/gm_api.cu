@@ -241,7 +241,7 @@ gpumcd_status ensure_slot(gpumcd_ctx *c, Slot &sl, int grid, int block) {
     if (!sl.ev1) CK(cudaEventCreate(&sl.ev1));
     if (!sl.done) CK(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
     if (!c->configured) {
-        CK(transport_configure(block));
+        CK(transport_configure());
         c->configured = true;
     }
     return GPUMCD_OK;
@@ -334,8 +334,8 @@ gpumcd_status gpumcd_init(gpumcd_ctx **out, int32_t device, uint64_t hbm_budget_
         delete c;
         return cuda_status(e);
     }
-    c->launch.block_threads = 512;
-    c->launch.blocks_per_sm = 2;
+    c->launch.block_threads = 1024;
+    c->launch.blocks_per_sm = 1;
     c->launch.stack_capacity = 512;
     c->launch.switch_high = 320;
     c->launch.refill_low = 16;
@@ -868,6 +868,7 @@ gpumcd_status seq_start(gpumcd_ctx *c, Slot &sl, int32_t n_plans, const int32_t 
     }
     Control *dc = (Control *)sl.control.p;
     A.tables = (const float *)c->tab.p;
+    A.tab_bytes = tab_bytes(c->n_mat);
     A.phys = c->dphys;
     A.plans = (const PlanDev *)sl.plandev.p;
     A.n_plans = n_plans;
@@ -878,8 +879,8 @@ gpumcd_status seq_start(gpumcd_ctx *c, Slot &sl, int32_t n_plans, const int32_t 
     A.switch_high = c->launch.switch_high;
     A.refill_low = c->launch.refill_low;
     A.refill_period = c->launch.refill_period;
-    // the phase-space kernel is compiled for up to 512 threads x 2 CTAs per SM, alone
-    if (A.phsp && (c->launch.blocks_per_sm > 2 || c->launch.refill_period != 1u ||
+    // the phase-space kernel is its own instantiation, without the other special ones
+    if (A.phsp && (c->launch.refill_period != 1u ||
                    (c->launch.flags & (GPUMCD_LAUNCH_PROFILE | GPUMCD_LAUNCH_WARP_AGGREGATE | GPUMCD_LAUNCH_KERMA))))
         return GPUMCD_ERR_INVALID_ARG;
     A.chunk = c->launch.chunk;
@@ -1316,27 +1317,19 @@ gpumcd_status gpumcd_set_launch(gpumcd_ctx *c, const gpumcd_launch *l) {
     if (l->overflow_capacity) n.overflow_capacity = l->overflow_capacity;
     n.flags = l->flags;
     if (l->refill_period) n.refill_period = l->refill_period;
-    if (n.block_threads % 32 || n.block_threads < 32 || n.block_threads > 512) return GPUMCD_ERR_INVALID_ARG;
+    if (n.block_threads % 32 || n.block_threads < 32 || n.block_threads > 1024) return GPUMCD_ERR_INVALID_ARG;
     if (n.blocks_per_sm < 1 || n.blocks_per_sm > 4) return GPUMCD_ERR_INVALID_ARG;
-    // supported (threads, CTAs/SM) pairs follow the kernel's launch-bound variants
-    const bool ok = (n.blocks_per_sm == 1 && n.block_threads <= 512) ||
-                    (n.blocks_per_sm == 2 && n.block_threads <= 512) ||
-                    (n.blocks_per_sm >= 3 && n.block_threads <= 256);
-    if (!ok) return GPUMCD_ERR_INVALID_ARG;
+    // every kernel is built for at most 1024 threads per SM (64 registers each)
+    if (n.block_threads * n.blocks_per_sm > 1024) return GPUMCD_ERR_INVALID_ARG;
     if (n.stack_capacity < 128 || n.stack_capacity > (1u << 16)) return GPUMCD_ERR_INVALID_ARG;
     if (n.switch_high < 32 || n.switch_high > n.stack_capacity) return GPUMCD_ERR_INVALID_ARG;
     if (n.refill_low > 32 || n.chunk < 1 || n.chunk > 4096) return GPUMCD_ERR_INVALID_ARG;
     if (n.overflow_capacity < 64 || n.overflow_capacity > (1u << 26)) return GPUMCD_ERR_INVALID_ARG;
-    // the profiling and warp-aggregating kernels are instantiated for up to
-    // 512 threads x 2 CTAs per SM, and not together
-    if ((n.flags & (GPUMCD_LAUNCH_PROFILE | GPUMCD_LAUNCH_WARP_AGGREGATE)) && n.blocks_per_sm > 2)
-        return GPUMCD_ERR_INVALID_ARG;
-    if ((n.flags & GPUMCD_LAUNCH_PROFILE) && (n.flags & GPUMCD_LAUNCH_WARP_AGGREGATE)) return GPUMCD_ERR_INVALID_ARG;
-    // the refill-policy ablation kernel and the photon-only kernel: 512 threads
-    // x 2 CTAs per SM at most, each alone
+    // the profiling, warp-aggregating, refill-policy and photon-only kernels
+    // are separate instantiations: at most one of them at a time
     const int special = ((n.flags & GPUMCD_LAUNCH_PROFILE) != 0u) + ((n.flags & GPUMCD_LAUNCH_WARP_AGGREGATE) != 0u) +
                         (n.refill_period != 1u) + ((n.flags & GPUMCD_LAUNCH_KERMA) != 0u);
-    if (special > 1 || (special == 1 && n.blocks_per_sm > 2)) return GPUMCD_ERR_INVALID_ARG;
+    if (special > 1) return GPUMCD_ERR_INVALID_ARG;
     c->launch = n;
     return GPUMCD_OK;
 }
@@ -1350,11 +1343,11 @@ gpumcd_status gpumcd_get_launch(gpumcd_ctx *c, gpumcd_launch *l) {
 gpumcd_status gpumcd_get_tables(gpumcd_ctx *c, int32_t which, float *out, int32_t *count) {
     if (!c || !count) return GPUMCD_ERR_INVALID_ARG;
     if (!c->tables) return GPUMCD_ERR_STATE;
-    int off = 0, n = 0;
-    if (which == 0) { off = TAB_PH; n = NMAT * 3 * G; }
-    else if (which == 1) { off = TAB_EL; n = NMAT * 4 * G; }
-    else if (which == 2) { off = TAB_MS; n = G_MS; }
-    else if (which == 3) { n = 2 * G; }
+    int n = 0;
+    if (which == 0) n = NMAT * 3 * G;
+    else if (which == 1) n = NMAT * 4 * G;
+    else if (which == 2) n = G_MS;
+    else if (which == 3) n = 2 * G;
     else return GPUMCD_ERR_INVALID_ARG;
     *count = n;
     if (!out) return GPUMCD_OK;
@@ -1368,8 +1361,17 @@ gpumcd_status gpumcd_get_tables(gpumcd_ctx *c, int32_t which, float *out, int32_
         dev_free(c, tmp);
         return cuda_status(e);
     }
-    CK(cudaMemcpyAsync(out, (const float *)c->tab.p + off, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream));
+    // the device keeps one block per material; the diagnostic layout is per table kind
+    std::vector<float> all(TAB_FLOATS);
+    CK(cudaMemcpyAsync(all.data(), c->tab.p, TAB_BYTES, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (which == 2) {
+        memcpy(out, all.data() + TAB_MS, (size_t)G_MS * 4);
+    } else {
+        const int k = which == 0 ? 3 : 4;
+        for (int m = 0; m < NMAT; ++m)
+            memcpy(out + (size_t)m * k * G, all.data() + (which == 0 ? tab_ph(m) : tab_el(m)), (size_t)k * G * 4);
+    }
     return GPUMCD_OK;
 }
 

@@ -35,14 +35,23 @@ static_assert((GPUMCD_MAX_PLANS_PER_RUN & (GPUMCD_MAX_PLANS_PER_RUN - 1)) == 0, 
 constexpr double MS_G_MIN = 1e-8;  // paths below this many transport mean free paths: no deflection
 constexpr double MS_G_MAX = 20.0;  // paths above: isotropic
 
-// Table layout in floats (global memory, staged whole into shared memory).
-constexpr int TAB_PH = 0;                       // [mat][mu_tot, mu_C, mu_pe][G]   cm^2/g
-constexpr int TAB_EL = TAB_PH + NMAT * 3 * G;   // [mat][L, S_hard, S_brem, l1inv][G]
-constexpr int TAB_MS = TAB_EL + NMAT * 4 * G;   // [G_MS] ln a over ln G1
-constexpr int TAB_BREM = TAB_MS + G_MS;         // [mat][cA, c1] bremsstrahlung shape
-constexpr int TAB_FLOATS = TAB_BREM + 4 * NMAT; // multiple of 4 floats (16 bytes)
+// Table layout in floats (global memory; a CTA stages the part it needs into
+// shared memory): the multiple-scattering table, the bremsstrahlung shape
+// constants, then one block per material holding its photon tables
+// [mu_tot, mu_C, mu_pe][G] (cm^2/g) and its electron tables
+// [L, S_hard, S_brem, l1inv][G].  The loaded materials come first, so their
+// blocks and everything before them are one contiguous range.
+constexpr int TAB_MS = 0;                            // [G_MS] ln a over ln G1
+constexpr int TAB_BREM = TAB_MS + G_MS;              // [mat][cA, c1] bremsstrahlung shape
+constexpr int TAB_MAT = TAB_BREM + 4 * NMAT;         // first material block
+constexpr int TAB_MAT_FLOATS = 7 * G;                // 3 photon + 4 electron tables
+constexpr int TAB_FLOATS = TAB_MAT + NMAT * TAB_MAT_FLOATS;
 constexpr int TAB_BYTES = TAB_FLOATS * 4;
-static_assert(TAB_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
+__host__ __device__ constexpr int tab_ph(int m) { return TAB_MAT + m * TAB_MAT_FLOATS; }          // photon tables of m
+__host__ __device__ constexpr int tab_el(int m) { return TAB_MAT + m * TAB_MAT_FLOATS + 3 * G; }  // electron tables of m
+// bytes of the tables of materials 0 .. n-1 and what precedes them (what a CTA stages)
+__host__ __device__ constexpr uint32_t tab_bytes(int n) { return 4u * (uint32_t)(TAB_MAT + n * TAB_MAT_FLOATS); }
+static_assert(tab_bytes(1) % 16 == 0 && (4 * TAB_MAT_FLOATS) % 16 == 0, "bulk copies move multiples of 16 bytes");
 
 constexpr int MAJ_FLOATS = 2 * G;  // per phantom: photon majorant | electron majorant
 
@@ -129,7 +138,8 @@ struct TransportArgs {
     uint32_t stack_cap, switch_high, refill_low, chunk;
     uint32_t flags;
     uint32_t refill_period;            // 1: refill every pass; N: every N-th pass or when empty
-    uint32_t phsp, pad_phsp;           // a plan of the launch has a phase-space source
+    uint32_t phsp;                     // a plan of the launch has a phase-space source
+    uint32_t tab_bytes;                // bytes of tables staged into shared memory (the loaded materials')
     unsigned long long *counters;      // run counters (see CNT_*)
     int32_t *error;                    // device status word
 };

@@ -41,8 +41,8 @@ cudaError_t launch_philox(const uint32_t *ctr, uint2 key, uint64_t n, int curand
                           cudaStream_t s);
 
 // Transport (gm_transport.cu).
-size_t transport_smem_bytes(int block_threads);
-cudaError_t transport_configure(int block_threads);
+size_t transport_smem_bytes(uint32_t tab_bytes);
+cudaError_t transport_configure();
 cudaError_t launch_transport(const TransportArgs &a, int grid, int block, int blocks_per_sm, cudaStream_t s);
 cudaError_t launch_debug_sample(const float *tab, const Phys &phys, int kind, float p0, int material,
                                 const float *spec, int n_spec, uint64_t n, uint64_t seed, float *out,

@@ -182,9 +182,9 @@ __global__ void k_build_tables(const MatDev *mats, int n_mat, double p0, double 
             mc = (float)c;
             mp = (float)pe;
         }
-        tab[TAB_PH + (m * 3 + 0) * G + i] = mt;
-        tab[TAB_PH + (m * 3 + 1) * G + i] = mc;
-        tab[TAB_PH + (m * 3 + 2) * G + i] = mp;
+        tab[tab_ph(m) + 0 * G + i] = mt;
+        tab[tab_ph(m) + 1 * G + i] = mc;
+        tab[tab_ph(m) + 2 * G + i] = mp;
     } else if (tid < n_ph + n_el) {
         const int t = tid - n_ph;
         const int m = t / G, i = t % G;
@@ -198,10 +198,10 @@ __global__ void k_build_tables(const MatDev *mats, int n_mat, double p0, double 
             H = (float)(hard + moller_hard(mats[m], T, t_c));
             M = (float)ms_l1inv(mats[m], T);
         }
-        tab[TAB_EL + (m * 4 + 0) * G + i] = L;
-        tab[TAB_EL + (m * 4 + 1) * G + i] = H;
-        tab[TAB_EL + (m * 4 + 2) * G + i] = B;
-        tab[TAB_EL + (m * 4 + 3) * G + i] = M;
+        tab[tab_el(m) + 0 * G + i] = L;
+        tab[tab_el(m) + 1 * G + i] = H;
+        tab[tab_el(m) + 2 * G + i] = B;
+        tab[tab_el(m) + 3 * G + i] = M;
     } else if (tid < n_ph + n_el + G_MS) {
         const int i = tid - n_ph - n_el;
         const double lg = log(MS_G_MIN) + (log(MS_G_MAX) - log(MS_G_MIN)) * i / (G_MS - 1);
@@ -279,8 +279,8 @@ __global__ void k_majorants(const float *tab, const unsigned int *rho_max_bits, 
     for (int m = 0; m < n_mat; ++m) {
         const float r = __uint_as_float(rho_max_bits[m]);
         if (r <= 0.f) continue;
-        mp = fmaxf(mp, r * tab[TAB_PH + (m * 3 + 0) * G + i]);
-        me = fmaxf(me, r * tab[TAB_EL + (m * 4 + 1) * G + i]);
+        mp = fmaxf(mp, r * tab[tab_ph(m) + i]);
+        me = fmaxf(me, r * tab[tab_el(m) + 1 * G + i]);
     }
     maj[i] = mp;
     const int lane = i & 31, w = i >> 5;

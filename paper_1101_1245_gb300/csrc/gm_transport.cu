@@ -445,7 +445,7 @@ __device__ __forceinline__ bool photon_flight(const TransportArgs &A, const Smem
     const uint32_t vw = __ldg(P.vox + idx);
     const int m = vw & (NMAT - 1);  // ids < NMAT (checked when packed): in range by construction
     const float rho = (float)(vw >> 4) * kRhoQ;
-    const float *tp = S.tab + TAB_PH + m * 3 * G;
+    const float *tp = S.tab + tab_ph(m);
     const bool pair_open = p.E > ph.two_mc2_q;
     float mu = rho * interp(tp, xp);
     if (!pair_open) mu = rho * (interp(tp + G, xp) + interp(tp + 2 * G, xp));
@@ -465,7 +465,7 @@ __device__ __forceinline__ void photon_interact(const TransportArgs &A, const Sm
     const uint32_t vw = __ldg(P.vox + idx);
     const int m = vw & (NMAT - 1);
     const float rho = (float)(vw >> 4) * kRhoQ;
-    const float *tp = S.tab + TAB_PH + m * 3 * G;
+    const float *tp = S.tab + tab_ph(m);
     const bool pair_open = p.E > ph.two_mc2_q;
     float mu = rho * interp(tp, xp);
     if (!pair_open) mu = rho * (interp(tp + G, xp) + interp(tp + 2 * G, xp));
@@ -577,7 +577,7 @@ __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, in
         p.act = false;
         return false;
     }
-    const float *te = S.tab + TAB_EL + m0 * 4 * G;
+    const float *te = S.tab + tab_el(m0);
     const float T = (float)p.E * kQf;
     const float xe = fmaf(__log2f((float)p.E), ph.grid.el_a, ph.grid.el_bq);
     const float L0 = rho0 * interp(te, xe);
@@ -659,7 +659,7 @@ __device__ __forceinline__ void hard_event(const TransportArgs &A, const Smem &S
     const uint32_t vw1 = __ldg(P.vox + idx1);
     const int m1 = vw1 & (NMAT - 1);
     const float rho1 = (float)(vw1 >> 4) * kRhoQ;
-    const float *t1 = S.tab + TAB_EL + m1 * 4 * G;
+    const float *t1 = S.tab + tab_el(m1);
     const float xe1 = fmaf(__log2f((float)e1), ph.grid.el_a, ph.grid.el_bq);
     const float T1 = (float)e1 * kQf;
     // Moller needs T > 2 t_c and bremsstrahlung T > k_c (zero below, as in the
@@ -741,6 +741,13 @@ struct CtaFlags {
     int in_done[2];
     int prim_done[2];
 };
+
+// Shared memory of a CTA: the plan table, warp states, counters, ledgers, the
+// mbarrier and the source flags (fixed size, rounded up to 128 bytes), then the
+// tables staged by the bulk copy.
+constexpr size_t SMEM_FIXED = (sizeof(PlanDev) * GPUMCD_MAX_PLANS_PER_RUN + sizeof(WarpState) * MAX_WARPS +
+                               sizeof(unsigned long long) * (CNT_N + 3 * GPUMCD_MAX_PLANS_PER_RUN + 1) +
+                               sizeof(CtaFlags) + 127) / 128 * 128;
 
 // Move the top n records of stack `t` to the global overflow queue.  A full
 // queue sets GPUMCD_ERR_QUEUE_OVERFLOW: the run is then invalid and reported,
@@ -942,14 +949,16 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
 // sources; the production instantiations carry none of them.
 template <int MAXT, int MINB, bool PROF, bool AGG, bool SCHED, bool KERMA, bool PHSP>
 __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant__ TransportArgs A) {
+    // the fixed-size parts first, at offsets known at compile time; the tables
+    // of the loaded materials after them
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float *tab = (float *)smem_raw;
-    PlanDev *plans = (PlanDev *)(smem_raw + TAB_BYTES);
+    PlanDev *plans = (PlanDev *)smem_raw;
     WarpState *ws = (WarpState *)(plans + GPUMCD_MAX_PLANS_PER_RUN);
     unsigned long long *cnt = (unsigned long long *)(ws + MAX_WARPS);
     unsigned long long *ledger = cnt + CNT_N;
     unsigned long long *mbar = ledger + 3 * GPUMCD_MAX_PLANS_PER_RUN;
     CtaFlags *flags = (CtaFlags *)(mbar + 1);
+    float *tab = (float *)(smem_raw + SMEM_FIXED);
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int gw = blockIdx.x * (blockDim.x >> 5) + w;
@@ -960,12 +969,12 @@ __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant_
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)),
-                     "r"((uint32_t)TAB_BYTES)
+                     "r"(A.tab_bytes)
                      : "memory");
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                 smem_addr(tab)),
-            "l"(A.tables), "r"((uint32_t)TAB_BYTES), "r"(smem_addr(mbar))
+            "l"(A.tables), "r"(A.tab_bytes), "r"(smem_addr(mbar))
             : "memory");
     }
     // every entry is set (unused ones copy plan 0), so any masked plan index
@@ -1126,13 +1135,18 @@ __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant_
         if (ledger[i]) atomicAdd(&plans[i / 3].ledger[i % 3], ledger[i]);
 }
 
-size_t transport_smem_bytes(int /*block_threads*/) {
-    return (size_t)TAB_BYTES + sizeof(PlanDev) * GPUMCD_MAX_PLANS_PER_RUN + sizeof(WarpState) * MAX_WARPS +
-           sizeof(unsigned long long) * (CNT_N + 3 * GPUMCD_MAX_PLANS_PER_RUN + 1) + sizeof(CtaFlags);
-}
+size_t transport_smem_bytes(uint32_t tab_bytes) { return (size_t)SMEM_FIXED + tab_bytes; }
 
-// Instantiations by launch bound (threads per CTA, CTAs per SM): the bound
-// sets the register budget, so the resident-CTA count is a launch choice.
+// Instantiations by register budget.  A launch bound (threads, CTAs) caps the
+// registers at 65536 / (threads x CTAs), and a kernel built for a budget runs
+// any launch with no more threads per CTA and no more threads per SM than its
+// bound: 128 registers up to 512 threads per SM, 80 up to 768, 64 up to 1024.
+// The 64-register kernel is the production one at its default shape, 1024
+// threads x 1 CTA per SM: the same 32 warps per SM as 512 x 2 but one copy of
+// the tables in shared memory, which leaves the larger L1 carve-out to the
+// voxel words, majorants and stack records (5-6% faster on the batched
+// workload than 512 x 2 in a same-box A/B).  The profile, aggregation,
+// refill-policy, photon-only and phase-space kernels are built for it too.
 typedef void (*TransportKernel)(const TransportArgs);
 struct Variant {
     int max_threads, min_blocks;
@@ -1142,29 +1156,28 @@ struct Variant {
 static const Variant kVariants[] = {
     {512, 1, false, false, false, false, false, k_transport<512, 1, false, false, false, false, false>},
     {384, 2, false, false, false, false, false, k_transport<384, 2, false, false, false, false, false>},
-    {512, 2, false, false, false, false, false, k_transport<512, 2, false, false, false, false, false>},
-    {256, 3, false, false, false, false, false, k_transport<256, 3, false, false, false, false, false>},
-    {256, 4, false, false, false, false, false, k_transport<256, 4, false, false, false, false, false>},
-    {512, 2, true, false, false, false, false, k_transport<512, 2, true, false, false, false, false>},
-    {512, 2, false, true, false, false, false, k_transport<512, 2, false, true, false, false, false>},
-    {512, 2, false, false, true, false, false, k_transport<512, 2, false, false, true, false, false>},
-    {512, 2, false, false, false, true, false, k_transport<512, 2, false, false, false, true, false>},
-    {512, 2, false, false, false, false, true, k_transport<512, 2, false, false, false, false, true>},
+    {1024, 1, false, false, false, false, false, k_transport<1024, 1, false, false, false, false, false>},
+    {1024, 1, true, false, false, false, false, k_transport<1024, 1, true, false, false, false, false>},
+    {1024, 1, false, true, false, false, false, k_transport<1024, 1, false, true, false, false, false>},
+    {1024, 1, false, false, true, false, false, k_transport<1024, 1, false, false, true, false, false>},
+    {1024, 1, false, false, false, true, false, k_transport<1024, 1, false, false, false, true, false>},
+    {1024, 1, false, false, false, false, true, k_transport<1024, 1, false, false, false, false, true>},
 };
 
+// The first variant (most registers first) whose bound covers the launch.
 static TransportKernel pick_variant(int block, int blocks_per_sm, bool prof, bool agg, bool sched, bool kerma,
                                     bool phsp) {
     for (const Variant &v : kVariants)
         if (v.prof == prof && v.agg == agg && v.sched == sched && v.kerma == kerma && v.phsp == phsp &&
-            block <= v.max_threads && blocks_per_sm <= v.min_blocks)
+            block <= v.max_threads && block * blocks_per_sm <= v.max_threads * v.min_blocks)
             return v.fn;
     return nullptr;
 }
 
-cudaError_t transport_configure(int block_threads) {
+cudaError_t transport_configure() {
     for (const Variant &v : kVariants) {
         cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)transport_smem_bytes(block_threads));
+                                             (int)transport_smem_bytes(TAB_BYTES));
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -1175,7 +1188,8 @@ cudaError_t launch_transport(const TransportArgs &a, int grid, int block, int bl
                                       (a.flags & GPUMCD_LAUNCH_WARP_AGGREGATE) != 0u, a.refill_period != 1u,
                                       (a.flags & GPUMCD_LAUNCH_KERMA) != 0u, a.phsp != 0u);
     if (!fn) return cudaErrorInvalidConfiguration;
-    fn<<<grid, block, transport_smem_bytes(block), s>>>(a);
+    if (a.tab_bytes < tab_bytes(1) || a.tab_bytes > (uint32_t)TAB_BYTES) return cudaErrorInvalidValue;
+    fn<<<grid, block, transport_smem_bytes(a.tab_bytes), s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1212,20 +1226,10 @@ __global__ void k_debug_sample(const float *tabg, Phys ph, int kind, float p0, i
         v = sample_brem(p, P, p0, ph.k_c, __ldg(tabg + TAB_BREM + 2 * material),
                         __ldg(tabg + TAB_BREM + 2 * material + 1), &wd, &capped);
     } else if (kind == 4) {
-        // the ms table is read from global memory here
+        // the transport's own ms_mu, given the tables in global memory instead
+        // of their shared-memory copy (the same word of the draw as a step uses)
         const uint4 r = draw4(p, P);
-        if (p0 < (float)MS_G_MIN) v = 0.f;
-        else if (p0 > (float)MS_G_MAX) v = u01(r.z);
-        else {
-            const float x = fmaf(__log2f(p0), ph.grid.ms_a, ph.grid.ms_b);
-            const float xc = fminf(fmaxf(x, 0.0f), (float)(G_MS - 1));
-            const int k = min((int)xc, G_MS - 2);
-            const float f = xc - k;
-            const float la = fmaf(f, __ldg(tabg + TAB_MS + k + 1) - __ldg(tabg + TAB_MS + k), __ldg(tabg + TAB_MS + k));
-            const float a = __expf(la);
-            const float z = u01(r.z);
-            v = a * z / (1.0f + a - z);
-        }
+        v = ms_mu(tabg, ph.grid, p0, u01(r.z));
     } else if (kind == 5) {
         const uint4 r = draw4(p, P);
         v = sample_spectrum(P, u01(r.z));

@@ -162,15 +162,15 @@ def test_cached_blocks_yield_to_the_budget():
 
 def test_refill_policy_validation():
     """A refill policy other than every pass, and the photon-only mode, each run
-    their own kernel, compiled for up to 512 threads x 2 CTAs per SM and alone
-    (without the profile, the warp-aggregated deposits or each other)."""
+    their own kernel, alone (without the profile, the warp-aggregated deposits
+    or each other); like every kernel, at most 1024 threads per SM."""
     ctx = make_ctx()
-    for bad in (dict(refill_period=4, block_threads=256, blocks_per_sm=3),
+    for bad in (dict(refill_period=4, block_threads=512, blocks_per_sm=3),
                 dict(refill_period=g.REFILL_WHEN_EMPTY, flags=g.LAUNCH_PROFILE),
                 dict(refill_period=16, flags=g.LAUNCH_WARP_AGGREGATE),
                 dict(refill_period=4, flags=g.LAUNCH_KERMA),
                 dict(flags=g.LAUNCH_KERMA | g.LAUNCH_PROFILE),
-                dict(flags=g.LAUNCH_KERMA, block_threads=256, blocks_per_sm=3)):
+                dict(flags=g.LAUNCH_KERMA, block_threads=1024, blocks_per_sm=2)):
         with pytest.raises(g.GpumcdError) as e:
             ctx.set_launch(**bad)
         assert e.value.status == g.ERR_INVALID_ARG
@@ -178,27 +178,30 @@ def test_refill_policy_validation():
     assert ctx.get_launch()["refill_period"] == 8
     ctx.set_launch(refill_period=1, flags=0)
     assert ctx.get_launch()["refill_period"] == 1
+    ctx.set_launch(flags=g.LAUNCH_KERMA, block_threads=256, blocks_per_sm=3)
+    ctx.set_launch(flags=0, block_threads=1024, blocks_per_sm=1)
     ctx.close()
 
 
 def test_launch_flags_select_compiled_kernels():
     """The cycle profile and warp-aggregated deposits are separate kernel
-    instantiations (512 threads x 2 CTAs per SM): combining them, or asking
-    for more CTAs per SM, is rejected; each alone runs and gives the plain
-    kernel's tally."""
+    instantiations: combining them, or asking for more than 1024 threads per
+    SM, is rejected; each alone runs and gives the plain kernel's tally, at
+    the default shape and at 512 threads x 2 CTAs per SM."""
     ctx = make_ctx()
     with pytest.raises(g.GpumcdError) as e:
         ctx.set_launch(flags=g.LAUNCH_PROFILE | g.LAUNCH_WARP_AGGREGATE)
     assert e.value.status == g.ERR_INVALID_ARG
     for flag in (g.LAUNCH_PROFILE, g.LAUNCH_WARP_AGGREGATE):
         with pytest.raises(g.GpumcdError) as e:
-            ctx.set_launch(flags=flag, block_threads=256, blocks_per_sm=3)
+            ctx.set_launch(flags=flag, block_threads=512, blocks_per_sm=3)
         assert e.value.status == g.ERR_INVALID_ARG
     ph = W.homogeneous((24, 24, 24), 0.5, W.MAT_WATER, 1.0)
     src = W.square_field(W.ELECTRON, 8.0, ph, 4.0)
     doses = []
-    for flag in (0, g.LAUNCH_PROFILE, g.LAUNCH_WARP_AGGREGATE | g.LAUNCH_GRAPH):
-        ctx.set_launch(flags=flag, block_threads=512, blocks_per_sm=2)
+    for flag, bt, bps in ((0, 1024, 1), (g.LAUNCH_PROFILE, 512, 2), (g.LAUNCH_WARP_AGGREGATE | g.LAUNCH_GRAPH, 1024, 1),
+                          (g.LAUNCH_PROFILE, 1024, 1)):
+        ctx.set_launch(flags=flag, block_threads=bt, blocks_per_sm=bps)
         pid = ctx.create_phantom(ph)
         doses.append(ctx.simulate(pid, src, 20_000, 3, nvox=ph.nvox).dose)
         ctx.destroy_phantom(pid)

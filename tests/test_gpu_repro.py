@@ -50,9 +50,9 @@ SOURCES = {
 
 
 def _phsp_kernel_accepts(launch) -> bool:
-    """A grouped spectrum runs the phase-space kernel: at most 2 CTAs per SM,
-    no profile or aggregation flag, refill at every pass."""
-    return (launch.get("blocks_per_sm", 2) <= 2 and launch.get("refill_period", 1) == 1
+    """A grouped spectrum runs the phase-space kernel: no profile or
+    aggregation flag, refill at every pass."""
+    return (launch.get("refill_period", 1) == 1
             and not launch.get("flags", 0) & (g.LAUNCH_WARP_AGGREGATE | g.LAUNCH_PROFILE))
 
 
@@ -68,6 +68,8 @@ def reference():
 @pytest.mark.parametrize("kind", ["electron", "photon", "grouped"])
 @pytest.mark.parametrize("launch", [
     dict(),
+    dict(block_threads=512, blocks_per_sm=2),
+    dict(block_threads=512, blocks_per_sm=1),
     dict(block_threads=256, blocks_per_sm=2),
     dict(block_threads=128, blocks_per_sm=3, chunk=8, refill_low=30, switch_high=64,
          stack_capacity=128),
