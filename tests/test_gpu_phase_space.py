@@ -239,3 +239,28 @@ def test_grouped_spectrum_runs_the_phase_space_kernel(ctx):
     finally:
         ctx.set_launch(flags=0)
         ctx.destroy_phantom(pid)
+
+
+def test_grouped_spectrum_stratifies_blocks_beyond_2_to_24_histories(ctx):
+    """The strata of a grouped spectrum depend on h mod 2^16 and the block's own
+    draw, so they hold at any history index.  After 2^24 histories (where a
+    run-relative FP32 quantile would have lost a stratum's width), one more
+    whole aligned block takes every stratum once: its incident energy is
+    65536 times the spectrum's mean within a few widths of the spectrum, where
+    iid draws would scatter by ~350 MeV."""
+    edges, w = W.synthetic_6mv_spectrum(n_bins=64)
+    ph = W.homogeneous((8, 8, 8), 0.5, W.MAT_LUNG, 0.05)
+    src = W.Source(W.PHOTON, W.BEAM_PENCIL, center_cm=(2.0, 2.0), spectrum_edges=edges,
+                   spectrum_weights=w, energy_grouping=W.ENERGY_GROUPED)
+    pid = ctx.create_phantom(ph)
+    plan = ctx.plan_open(pid, src, 5, 16)
+    ctx.run([plan], [1 << 24])
+    e0 = ctx.plan_result(plan, 0.5)["e_incident"]
+    ctx.run([plan], [1 << 16])
+    st = ctx.plan_result(plan, 0.5)
+    assert st["histories"] == (1 << 24) + (1 << 16) and ledger_exact(st)
+    width = float(edges[-1] - edges[0])
+    got = (st["e_incident"] - e0) * Q
+    assert abs(got - 65536 * _mean_energy(edges, w)) <= 3.0 * width, (got, 65536 * _mean_energy(edges, w))
+    ctx.plan_close(plan)
+    ctx.destroy_phantom(pid)
