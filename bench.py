@@ -9,7 +9,8 @@ Default workload: the batched configuration, 64 independent uneven plans
 from a zeroed tally to s_0.5 <= 1% (gpumcd_run_to_uncertainty: a first round
 of the plan's own history count, then rounds sized by s ~ 1/sqrt(N)).  One
 step = all 64 plans to 1%.
-- value: the batched form, every round of all active plans in one launch
+- value: the batched form: in each round a plan given >= 2^23 histories runs in a
+  launch of its own, the other active plans share one launch
   sequence per particle type;
 - plain: the same plans one at a time with the same schedule (the same
   histories and, bit for bit, the same tallies);
@@ -535,20 +536,21 @@ def run_c4(args):
     def seeds(step):
         return [c4_seed(sp, rank, step) for sp in specs]
 
-    def batched(step):
+    def batched(step, target=TARGET):
         for p, sd in zip(plans, seeds(step)):
             ctx.plan_reset(p, sd, sh)
-        return ctx.run_to_uncertainty(plans, first, caps, TARGET, THRESHOLD, sh)
+        return ctx.run_to_uncertainty(plans, first, caps, target, THRESHOLD, sh)
 
-    def plain(step):
-        out = {"histories": [], "s_thr": [], "rounds": 0, "transport_ms": 0.0}
+    def plain(step, target=TARGET):
+        out = {"histories": [], "s_thr": [], "rounds": 0, "transport_ms": 0.0, "sequences": 0}
         for p, sd, f, c in zip(plans, seeds(step), first, caps):
             ctx.plan_reset(p, sd, sh)
-            r = ctx.run_to_uncertainty([p], [f], [c], TARGET, THRESHOLD, sh)
+            r = ctx.run_to_uncertainty([p], [f], [c], target, THRESHOLD, sh)
             out["histories"] += r["histories"]
             out["s_thr"] += r["s_thr"]
             out["rounds"] += r["rounds"]
             out["transport_ms"] += r["transport_ms"]
+            out["sequences"] += r["sequences"]
         return out
 
     def timed(fn, step):
@@ -586,13 +588,11 @@ def run_c4(args):
                for t in (W.ELECTRON, W.PHOTON)}
     last = res[-1][1]
     ledger_ok = all(x["e_deposited"] + x["e_escaped"] + x["e_rest"] == x["e_incident"] for x in st)
-    # per plan, n_launches counts the launches of the sequences it ran in (its
-    # rounds, one launch each unless a queue overflowed): the folds; a round
-    # runs one sequence per particle type
+    # per plan, n_launches counts the launches of the sequences it ran in (one
+    # per round unless a queue overflowed): its folds
     folds = sum(x["n_launches"] for x in st)
-    transport_launches = sum(max((x["n_launches"] for x, sp in zip(st, specs) if sp.particle == t), default=0)
-                             for t in (W.ELECTRON, W.PHOTON))
-    launches = transport_launches + 2 * folds  # + the fold and s_thr kernels of every fold
+    transport_launches = last["sequences"]
+    launches = transport_launches + 3 * folds  # + the fold and two s_thr kernels of every fold
 
     # the plain form: the same plans one at a time, same seeds and schedule
     plain_runs = [timed(plain, i) for i in range(min(2, args.steps))]
@@ -601,6 +601,13 @@ def run_c4(args):
     plain_value = sum(sum(p[1]["histories"]) for p in plain_runs) / (sum(p[0] for p in plain_runs) / 1e3)
     batched_ms = statistics.median(r[0] for r in res[:len(plain_runs)])
     log(f"plain {plain_value:.3e} histories/s")
+    # one round at each plan's own history count (configuration 4 as written):
+    # a target every plan meets at once ends the run after its first round
+    one = [(timed(lambda i: batched(i, 1e9), 100 + i), timed(lambda i: plain(i, 1e9), 100 + i)) for i in range(3)]
+    first_round = {"histories": sum(first), "batched_ms": statistics.median(b[0] for b, _ in one),
+                   "plain_ms": statistics.median(p[0] for _, p in one)}
+    first_round["batched_over_plain"] = first_round["plain_ms"] / first_round["batched_ms"]
+    first_round["batched_value"] = first_round["histories"] / (first_round["batched_ms"] / 1e3)
 
     # the paper's timing workload, as a sub-record
     for p in plans:
@@ -659,8 +666,9 @@ def run_c4(args):
                        "target": f"s_0.5 <= {TARGET:g} per plan (mean sigma/D over voxels above 0.5 D_max)",
                        "schedule": "first round = the plan's own history count, then rounds sized by "
                                    "s ~ 1/sqrt(N) (gpumcd_run_to_uncertainty); at most 4e8 histories a plan",
-                       "form": "batched: each round of all active plans in one launch sequence per particle "
-                               "type (autotuned launch)",
+                       "form": "batched: in each round a plan given >= 2^23 histories runs in a launch of its "
+                               "own, the others share one launch sequence per particle type (autotuned launch)",
+                       "transport_sequences_per_step": last["sequences"],
                        "histories_per_step": statistics.median(hist_steps),
                        "rounds_per_step": last["rounds"],
                        "transport_ms_per_step": last["transport_ms"],
@@ -672,12 +680,15 @@ def run_c4(args):
                        "launch": tuned["launch"], "launch_graph": bool(args.graph),
                        "ledger_exact": ledger_ok},
             "plain": {"value": plain_value, "passes": len(plain_runs),
+                      "transport_ms_per_step": statistics.median(p[1]["transport_ms"] for p in plain_runs),
+                      "transport_sequences_per_step": plain_runs[0][1]["sequences"],
                       "ms_per_step": statistics.median(p[0] for p in plain_runs),
                       "batched_ms_same_seeds": batched_ms,
                       "batched_over_plain": statistics.median(p[0] for p in plain_runs) / batched_ms,
                       "same_histories_and_s_as_batched": same,
                       "form": "each plan alone, the same seeds and schedule (gpumcd_run_to_uncertainty "
-                              "with one plan)"},
+                              "with one plan)",
+                      "first_round_only": first_round},
             "served": served,
             "c2": c2,
             "roofline": roof,
@@ -1026,16 +1037,28 @@ def run_grouping(args):
                 src = W.polyenergetic_square(particle, ph)
             d = torch.zeros(ph.nvox, dtype=torch.float64, device="cuda")
             sg = torch.zeros_like(d)
+            # a one-record phase space of the same particle type: run beside a plan
+            # (one history), it puts the launch on the phase-space kernel, so the
+            # ungrouped spectrum can be timed on the grouped one's kernel too
+            rec = np.array([[ph.extent_cm[0] / 2, ph.extent_cm[1] / 2, 0.0, 0.0, 0.0, 1.0, 1.0]])
+            dummy = ctx.plan_open(pid, W.Source(particle, W.BEAM_PHASE_SPACE, phase_space=rec), 1, 8)
             out = {}
-            for label, grouping in (("ungrouped", W.ENERGY_UNGROUPED), ("grouped", W.ENERGY_GROUPED)):
+            forms = [("ungrouped", W.ENERGY_UNGROUPED, False), ("grouped", W.ENERGY_GROUPED, False)]
+            if kind == "spectrum":
+                forms.insert(1, ("ungrouped_phsp_kernel", W.ENERGY_UNGROUPED, True))
+            for label, grouping, with_dummy in forms:
                 src.energy_grouping = grouping
                 plan = ctx.plan_open(pid, src, pl.seed, 32)
 
                 def once():
                     ctx.plan_reset(plan, pl.seed)
+                    ctx.plan_reset(dummy, 1)
                     torch.cuda.synchronize()
                     ev[0].record()
-                    ctx.run([plan], [pl.n_histories])
+                    if with_dummy:
+                        ctx.run([plan, dummy], [pl.n_histories, 1])
+                    else:
+                        ctx.run([plan], [pl.n_histories])
                     st = ctx.plan_result(plan, 0.5, d.data_ptr(), sg.data_ptr())
                     ev[1].record()
                     torch.cuda.synchronize()
@@ -1051,6 +1074,7 @@ def run_grouping(args):
                               "ledger_exact": st["e_deposited"] + st["e_escaped"] + st["e_rest"] == st["e_incident"],
                               "dose": d.cpu().numpy(), "sigma": sg.cpu().numpy()}
                 ctx.plan_close(plan)
+            ctx.plan_close(dummy)
             ctx.destroy_phantom(pid)
             a, b = out["ungrouped"], out["grouped"]
             mask = a["dose"] > 0.1 * a["dose"].max()
@@ -1060,6 +1084,9 @@ def run_grouping(args):
                          "transport_ms": {k: v["transport_ms"] for k, v in out.items()},
                          "step_ms": {k: v["ms"] for k, v in out.items()},
                          "grouped_speedup": a["transport_ms"] / b["transport_ms"],
+                         "grouped_speedup_same_kernel": (out["ungrouped_phsp_kernel"]["transport_ms"]
+                                                         / b["transport_ms"]) if kind == "spectrum" else
+                         a["transport_ms"] / b["transport_ms"],
                          "electron_steps_per_history": {k: v["electron_steps_per_history"] for k, v in out.items()},
                          "ledger_exact": all(v["ledger_exact"] for v in out.values()),
                          "dose_3sigma_agreement": float(agree[mask].mean())})
@@ -1107,8 +1134,22 @@ def served_leg(ctx, phantoms, pids, args) -> dict:
                  rounds_in_flight=args.rounds_in_flight)
     for q in requests(rate):
         srv.submit(q)
-    srv.run(real_time=True)
+    results = srv.run(real_time=True)
     rep = srv.report()
+    # the same stream served first come first served, each request alone at the
+    # measured alone rate (a model from the requests' histories, not a run):
+    # what continuous batching changes in latency at the same throughput
+    import numpy as np
+    alone_rate = alone_h / alone_t if alone_t else None
+    fifo = None
+    if alone_rate:
+        t_free, lat = 0.0, []
+        for r in sorted(results, key=lambda r: r.arrival_s):
+            start = max(t_free, r.arrival_s)
+            t_free = start + r.histories / alone_rate
+            lat.append(t_free - r.arrival_s)
+        fifo = {"latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+                "basis": "each request's histories at the measured alone rate, in arrival order"}
     return {"target": args.target, "threshold": THRESHOLD,
             "capacity_value": rep_cal["histories_per_s"],
             "alone_value": alone_h / alone_t if alone_t else None,
@@ -1118,7 +1159,8 @@ def served_leg(ctx, phantoms, pids, args) -> dict:
             "requests": rep["requests"], "arrival_rate_per_s": rate,
             "rate_basis": "0.8 x the served capacity on the calibration set",
             "stream_value": rep["histories_per_s"], "latency_p50_s": rep["latency_p50_s"],
-            "latency_p99_s": rep["latency_p99_s"], "wall_s": rep["wall_s"], "rounds": rep["rounds"],
+            "latency_p99_s": rep["latency_p99_s"], "fifo_alone_model": fifo,
+            "wall_s": rep["wall_s"], "rounds": rep["rounds"],
             "folds": rep["folds"], "mean_histories_per_request": rep["histories"] / max(rep["requests"], 1),
             "s_thr_max": rep["s_thr_max"], "rounds_in_flight": args.rounds_in_flight,
             "round_histories": args.round_histories, "hbm_budget_gb": args.budget_gb,

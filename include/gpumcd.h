@@ -63,17 +63,14 @@ typedef int32_t gpumcd_status;
  * - a phase space's records are stably sorted by decreasing E at
  *   gpumcd_plan_open; history h takes record h mod n of the sorted list (ties
  *   keep their listed order);
- * - a spectrum is sampled stratified over aligned blocks of 2^16 histories:
- *   history h, j = h mod 2^16 in block k = h / 2^16, draws the cumulative-
- *   spectrum quantile (s + u)/2^16 with u its own uniform draw and stratum
- *   s = (64 bitrev10(j / 64) + j mod 64 + r_k) mod 2^16, r_k a uniform draw
- *   of the block keyed by the plan's seed.  64 consecutive histories take
- *   consecutive strata (similar energies), the chunks of 64 follow the
- *   bit-reversed order (a part of a block spreads over the whole spectrum),
- *   and a whole block takes every stratum once.  Over r_k each history's
- *   quantile is uniform, so any history count is unbiased; the energy
- *   depends on the history index alone, so the tally does not depend on how
- *   the histories are split into runs, batched or served;
+ * - a spectrum keeps its sample: each history draws its energy as it would
+ *   ungrouped (run on the same kernel, the tallies are equal bit for bit, and
+ *   they do not depend on how the histories are split); but each launch first
+ *   sorts its histories of the plan by energy (a counting sort over the
+ *   spectrum's bins, of at most 2^28 histories a launch; the rest are claimed
+ *   as numbered) and claims them in decreasing order, so the warps, and the
+ *   whole grid at any moment, start histories of similar energy, the longest
+ *   first;
  * - a monoenergetic beam is unchanged.
  * A launch holding a grouped spectral plan runs the phase-space kernel, with
  * its restrictions. */
@@ -313,8 +310,11 @@ gpumcd_status gpumcd_plan_result_host(gpumcd_ctx *ctx, int32_t plan_id, double t
 /* Runs plans to a target uncertainty (§II.D: s, the mean of sigma/D over the
  * voxels with dose above threshold_frac x D_max; the "1% uncertainty" of a
  * dose calculation).  All n_plans <= GPUMCD_MAX_PLANS_PER_RUN distinct plans
- * (host array plan_ids) run together in rounds, each round one gpumcd_run on
- * `stream` over the plans still above the target, followed by their folds.
+ * (host array plan_ids) run together in rounds over the plans still above the
+ * target, each round followed by their folds, all on `stream`.  In a round, a
+ * plan given at least 2^23 histories runs in a launch of its own; the others
+ * share one gpumcd_run (which saves a launch's fixed cost per plan, while
+ * plans that share a launch share the SMs' caches).
  * In the first round plan i runs first_histories[i] more histories; after
  * each round a plan with N histories and uncertainty s > target is given
  * enough to reach max(1.05 N (s/target)^2, 1.1 N), since s falls as 1/sqrt(N).
@@ -323,8 +323,9 @@ gpumcd_status gpumcd_plan_result_host(gpumcd_ctx *ctx, int32_t plan_id, double t
  * depends on its own results only, so running plans together or one by one
  * gives the same histories and, bit for bit, the same tallies.  Outputs (host,
  * optional): histories_out[i] the plan's total histories, s_thr_out[i] its
- * final s (infinity if no dose), *rounds_out the rounds run and
- * *transport_ms_out the device time of their transport launches.  Plans continue
+ * final s (infinity if no dose), *rounds_out the rounds run,
+ * *transport_ms_out the device time of their transport launches and
+ * *sequences_out the launch sequences they took.  Plans continue
  * from the histories they hold.  Errors: GPUMCD_ERR_INVALID_ARG (target <= 0,
  * threshold outside [0, 1], first_histories[i] = 0, max_histories[i] below
  * first_histories[i] or above 2^32, a repeated id), GPUMCD_ERR_NOT_FOUND,
@@ -334,7 +335,7 @@ gpumcd_status gpumcd_run_to_uncertainty(gpumcd_ctx *ctx, int32_t n_plans, const 
                                         const uint64_t *first_histories, const uint64_t *max_histories,
                                         double target_rel_unc, double threshold_frac, void *stream,
                                         uint64_t *histories_out, double *s_thr_out, uint32_t *rounds_out,
-                                        double *transport_ms_out);
+                                        double *transport_ms_out, uint32_t *sequences_out);
 
 /* Histories of a plan's finished sequences. */
 gpumcd_status gpumcd_plan_histories(gpumcd_ctx *ctx, int32_t plan_id, uint64_t *histories);

@@ -68,8 +68,7 @@ class SourceC(C.Structure):
     _fields_ = [("particle", C.c_int32), ("beam", C.c_int32), ("energy", C.c_double),
                 ("n_spec", C.c_int32), ("spec_edges", C.POINTER(C.c_double)),
                 ("spec_weights", C.POINTER(C.c_double)), ("cx", C.c_double), ("cy", C.c_double),
-                ("field", C.c_double), ("n_phsp", C.c_int32), ("phsp", C.POINTER(C.c_double)),
-                ("group", C.c_int32)]
+                ("field", C.c_double), ("n_phsp", C.c_int32), ("phsp", C.POINTER(C.c_double))]
 
 
 class Stats(C.Structure):
@@ -191,8 +190,9 @@ def phantom(ph, keep: _Keep) -> PhantomC:
 
 
 def source(src, keep: _Keep) -> SourceC:
-    """The C source (a grouped spectrum's strata follow from the history
-    index alone, see oracle.h)."""
+    """The C source.  Energy grouping (§IV) changes the sample of a phase space
+    only (its records sorted by decreasing energy, below); a grouped spectrum
+    draws as an ungrouped one does."""
     s = SourceC()
     s.particle = src.particle
     s.beam = src.beam
@@ -209,7 +209,6 @@ def source(src, keep: _Keep) -> SourceC:
     else:
         s.n_spec = 0
     grouped = getattr(src, "energy_grouping", 0) == 1
-    s.group = 1 if grouped and src.spectrum_edges is not None else 0
     ps = getattr(src, "phase_space", None)
     if ps is not None:
         a = np.ascontiguousarray(ps, dtype=np.float64).reshape(-1, 7)

@@ -68,19 +68,10 @@ typedef struct {
     double cx, cy, field;
     int32_t n_phsp;      /* beam 2: records */
     const double *phsp;  /* beam 2: [n_phsp][7] x, y, z (cm), ux, uy, uz, E (MeV) */
-    /* Energy grouping of a spectrum (§IV): with group = 1 and n_spec > 0,
-     * history h draws the cumulative-spectrum quantile (s + u)/2^16, u its
-     * uniform draw and s its stratum in the aligned block k = h / 2^16:
-     *   j = h mod 2^16, s = (64 bitrev10(j / 64) + j mod 64 + r_k) mod 2^16,
-     * r_k = the low 16 bits of the first word of Philox(counter (0, 0, 0, k),
-     * key = seed), a counter no particle uses.  So 64 consecutive histories
-     * take 64 consecutive strata (similar energies), the chunks of 64 follow
-     * the bit-reversed order (any prefix of a block spreads over the whole
-     * spectrum), a whole block takes every stratum once, and for every h the
-     * quantile is uniform on (0, 1] over r_k: any history count is unbiased.
-     * The energy depends on the history index and the seed alone.  (A grouped
-     * phase space is sorted by the caller.) */
-    int32_t group;
+    /* Energy grouping (§IV) changes no sample here: a grouped spectrum draws
+     * its energies as an ungrouped one does (the GPU orders the claims of its
+     * histories by energy, which leaves each history's draws unchanged), and a
+     * grouped phase space is sorted by the caller. */
 } om_source;
 
 typedef struct {

@@ -733,24 +733,7 @@ static void make_primary(ctx_t *c, const om_source *src, const double *cdf, uint
     p->u[0] = 0.0;
     p->u[1] = 0.0;
     p->u[2] = 1.0;
-    if (src->n_spec > 0 && src->group) {
-        /* energy grouping (§IV): stratum s of the aligned block of 2^16 histories
-         * holding h, rotated by the block's own draw (see om_source) */
-        const double u = uniform(s);
-        const uint32_t k = (uint32_t)(h >> 16), j = (uint32_t)(h & 0xFFFFu);
-        const uint32_t ctr[4] = {0u, 0u, 0u, k};
-        const uint32_t key[2] = {(uint32_t)c->seed, (uint32_t)(c->seed >> 32)};
-        uint32_t w[4];
-        om_philox4x32_10(ctr, key, w);
-        const uint32_t chunk = j >> 6;
-        uint32_t rev = 0;
-        for (int b = 0; b < 10; ++b) rev |= ((chunk >> b) & 1u) << (9 - b);
-        const uint32_t stratum = (64u * rev + (j & 63u) + (w[0] & 0xFFFFu)) & 0xFFFFu;
-        const double z = ((double)stratum + u) / 65536.0;
-        p->E = spectrum_at(src->n_spec, src->spec_edges, cdf, z);
-    } else {
-        p->E = src->n_spec > 0 ? sample_spectrum(s, src->n_spec, src->spec_edges, cdf) : src->energy;
-    }
+    p->E = src->n_spec > 0 ? sample_spectrum(s, src->n_spec, src->spec_edges, cdf) : src->energy;
     p->type = src->particle;
     p->lin = 1ull;
     p->draw = s->draw;

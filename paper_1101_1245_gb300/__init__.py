@@ -130,7 +130,7 @@ SIGNATURES = {
     "gpumcd_plan_result_host": (_ST, [_CTX, _I32, _D, _P, _P, C.POINTER(RunStats)]),
     "gpumcd_run_to_uncertainty": (_ST, [_CTX, _I32, C.POINTER(_I32), C.POINTER(_U64), C.POINTER(_U64), _D, _D,
                                         _P, C.POINTER(_U64), C.POINTER(_D), C.POINTER(C.c_uint32),
-                                        C.POINTER(_D)]),
+                                        C.POINTER(_D), C.POINTER(C.c_uint32)]),
     "gpumcd_plan_histories": (_ST, [_CTX, _I32, C.POINTER(_U64)]),
     "gpumcd_plan_result_noalloc": (_ST, [_CTX, _I32, _D, _P, _P, _P, C.POINTER(RunStats)]),
     "gpumcd_memory": (_ST, [_CTX, C.POINTER(_U64), C.POINTER(_U64)]),
@@ -374,7 +374,8 @@ class Context:
                            max_histories: Sequence[int], target: float, threshold: float = 0.5,
                            stream: int = 0) -> dict:
         """gpumcd_run_to_uncertainty: the plans' total histories, final s, the
-        rounds run and the device time of their transport launches."""
+        rounds run, the device time of their transport launches and the launch
+        sequences they took."""
         k = len(plans)
         ids = (_I32 * k)(*plans)
         first = (_U64 * k)(*first_histories)
@@ -383,9 +384,12 @@ class Context:
         s = (_D * k)()
         r = C.c_uint32()
         ms = _D()
+        q = C.c_uint32()
         _check(self._L.gpumcd_run_to_uncertainty(self.h, k, ids, first, mx, target, threshold, stream or None,
-                                                 h, s, C.byref(r), C.byref(ms)), "gpumcd_run_to_uncertainty")
-        return {"histories": list(h), "s_thr": list(s), "rounds": r.value, "transport_ms": ms.value}
+                                                 h, s, C.byref(r), C.byref(ms), C.byref(q)),
+               "gpumcd_run_to_uncertainty")
+        return {"histories": list(h), "s_thr": list(s), "rounds": r.value, "transport_ms": ms.value,
+                "sequences": q.value}
 
     def plan_histories(self, plan: int) -> int:
         h = _U64()

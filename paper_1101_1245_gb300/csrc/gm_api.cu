@@ -36,7 +36,7 @@ struct Plan {
     double energy, cx, cy, field;
     int32_t n_spec;
     uint32_t n_phsp = 0;     // phase-space records (held in `spec`)
-    bool e_group = false;    // spectrum sampled stratified per run, highest energies first
+    bool e_group = false;    // a spectrum grouped by energy: claimed highest energies first
     uint64_t seed;
     uint32_t W;
     uint64_t hist_sub = 0;   // histories handed to launch sequences (numbering of the next run)
@@ -65,6 +65,7 @@ struct Control {
 // gpumcd_submit on their own streams, so sequences can overlap on the device.
 struct Slot {
     DevBuf stacks, hard, queue[2][NT], control, plandev;
+    DevBuf order, gcount;  // claim orders of grouped spectra, and their sort's bin counts
     Control *h_control = nullptr;  // pinned: the control block after each launch
     PlanDev *h_plandev = nullptr;  // pinned: the sequence's plan table
     cudaStream_t own = nullptr;    // the slot's stream (asynchronous slots)
@@ -249,6 +250,8 @@ gpumcd_status ensure_slot(gpumcd_ctx *c, Slot &sl, int grid, int block) {
 
 void free_slot(gpumcd_ctx *c, Slot &sl) {
     if (sl.busy && sl.s) cudaStreamSynchronize(sl.s);
+    dev_free(c, sl.order);
+    dev_free(c, sl.gcount);
     dev_free(c, sl.stacks);
     dev_free(c, sl.hard);
     for (int b = 0; b < 2; ++b)
@@ -801,6 +804,10 @@ void seq_close(gpumcd_ctx *c, Slot &sl, gpumcd_status result, float ms) {
 }
 
 // Validate a run request and enqueue its first launch on stream s.
+// Histories of a grouped spectrum a launch sorts by energy at most (2^28, a
+// 1 GB claim order); the rest of a larger run is claimed as numbered.
+constexpr uint64_t kGroupSortMax = 1ull << 28;
+
 gpumcd_status seq_start(gpumcd_ctx *c, Slot &sl, int32_t n_plans, const int32_t *ids, const uint64_t *n_hist,
                         cudaStream_t s) {
     if (n_plans < 1 || n_plans > GPUMCD_MAX_PLANS_PER_RUN || !ids || !n_hist) return GPUMCD_ERR_INVALID_ARG;
@@ -860,7 +867,7 @@ gpumcd_status seq_start(gpumcd_ctx *c, Slot &sl, int32_t n_plans, const int32_t 
         d.e_group = p.e_group ? 1u : 0u;
         if (p.n_phsp || p.e_group) A.phsp = 1;
         d.hist_base = p.hist_sub;
-        d.n_hist = n_hist[i];
+        if (p.e_group) d.n_sorted = (uint32_t)std::min<uint64_t>(n_hist[i], kGroupSortMax);
         const int t = p.particle;
         A.prim_plan[t][A.n_prim_plans[t]] = (uint8_t)i;
         A.prim_off[t][A.n_prim_plans[t] + 1] = A.prim_off[t][A.n_prim_plans[t]] + n_hist[i];
@@ -887,6 +894,26 @@ gpumcd_status seq_start(gpumcd_ctx *c, Slot &sl, int32_t n_plans, const int32_t 
     A.flags = c->launch.flags;
     A.counters = dc->counters;
     A.error = &dc->error;
+
+    // spectra grouped by energy: sort each one's histories of this launch by
+    // energy, on the sequence's stream ahead of the launch
+    size_t n_order = 0;
+    for (int i = 0; i < n_plans; ++i) n_order += sl.h_plandev[i].e_group ? sl.h_plandev[i].n_sorted : 0u;
+    if (n_order > 0) {
+        if (sl.order.bytes < n_order * 4) {
+            dev_free(c, sl.order);  // the slot's last sequence has finished: nothing pending on it
+            ST(dev_alloc(c, sl.order, n_order * 4));
+        }
+        if (!sl.gcount.p) ST(dev_alloc(c, sl.gcount, GPUMCD_MAX_SPECTRUM_BINS * sizeof(unsigned)));
+        uint32_t *ord = (uint32_t *)sl.order.p;
+        for (int i = 0; i < n_plans; ++i) {
+            PlanDev &d = sl.h_plandev[i];
+            if (!d.e_group) continue;
+            d.order = ord;
+            CK(launch_group_order(d, d.n_sorted, (unsigned *)sl.gcount.p, ord, s));
+            ord += d.n_sorted;
+        }
+    }
 
     sl.s = s;
     sl.k = 0;
@@ -1162,10 +1189,14 @@ gpumcd_status gpumcd_plan_result_host(gpumcd_ctx *c, int32_t plan_id, double thr
     return GPUMCD_OK;
 }
 
+// Rounds of at least this many histories run in a launch of their own in
+// gpumcd_run_to_uncertainty (2^23).
+constexpr uint64_t kAloneHistories = 1ull << 23;
+
 gpumcd_status gpumcd_run_to_uncertainty(gpumcd_ctx *c, int32_t n_plans, const int32_t *ids,
                                         const uint64_t *first, const uint64_t *max_hist, double target,
                                         double thr, void *stream, uint64_t *hist_out, double *s_out,
-                                        uint32_t *rounds_out, double *transport_ms_out) {
+                                        uint32_t *rounds_out, double *transport_ms_out, uint32_t *sequences_out) {
     if (!c || n_plans < 1 || n_plans > GPUMCD_MAX_PLANS_PER_RUN || !ids || !first || !max_hist) return GPUMCD_ERR_INVALID_ARG;
     if (!(target > 0.0) || !(thr >= 0.0 && thr <= 1.0)) return GPUMCD_ERR_INVALID_ARG;
     std::vector<uint64_t> done(n_plans), goal(n_plans);
@@ -1183,7 +1214,7 @@ gpumcd_status gpumcd_run_to_uncertainty(gpumcd_ctx *c, int32_t n_plans, const in
         goal[i] = done[i] + first[i];
     }
     std::vector<char> active(n_plans, 1);
-    uint32_t rounds = 0;
+    uint32_t rounds = 0, sequences = 0;
     double transport_ms = 0.0;
     for (;;) {
         // this round: every active plan runs up to its goal, in whole multiples of
@@ -1203,21 +1234,44 @@ gpumcd_status gpumcd_run_to_uncertainty(gpumcd_ctx *c, int32_t n_plans, const in
             rn.push_back(n);
         }
         if (rid.empty()) break;
-        // a round is one sequence per particle type: its device time is the
-        // growth of one plan's transport time per type
-        double before[2] = {-1.0, -1.0};
-        int32_t probe[2] = {-1, -1};
-        for (int32_t id : rid) {
-            const Plan &pl = c->plans.at(id);
-            const int t = pl.particle == GPUMCD_ELECTRON ? 1 : 0;
-            if (probe[t] < 0) {
-                probe[t] = id;
-                before[t] = pl.acc.transport_ms;
+        // A plan whose round holds at least kAloneHistories runs in a launch of
+        // its own; the others share one launch sequence per particle type.
+        // Sharing saves the fixed cost of a launch (its drain, about half a
+        // millisecond) but mixes the plans' phantoms and tallies in the SMs'
+        // L1; for rounds this large the launch costs < 1% and the mix more.
+        std::vector<int32_t> sid;
+        std::vector<uint64_t> sn;
+        for (size_t r = 0; r < rid.size(); ++r) {
+            if (rn[r] >= kAloneHistories) {
+                const double before = c->plans.at(rid[r]).acc.transport_ms;
+                ST(gpumcd_run(c, 1, &rid[r], &rn[r], stream));
+                transport_ms += c->plans.at(rid[r]).acc.transport_ms - before;
+                ++sequences;
+            } else {
+                sid.push_back(rid[r]);
+                sn.push_back(rn[r]);
             }
         }
-        ST(gpumcd_run(c, (int32_t)rid.size(), rid.data(), rn.data(), stream));
-        for (int t = 0; t < 2; ++t)
-            if (probe[t] >= 0) transport_ms += c->plans.at(probe[t]).acc.transport_ms - before[t];
+        if (!sid.empty()) {
+            // one sequence per particle type: its device time is the growth of
+            // one plan's transport time per type
+            double before[2] = {-1.0, -1.0};
+            int32_t probe[2] = {-1, -1};
+            for (int32_t id : sid) {
+                const Plan &pl = c->plans.at(id);
+                const int t = pl.particle == GPUMCD_ELECTRON ? 1 : 0;
+                if (probe[t] < 0) {
+                    probe[t] = id;
+                    before[t] = pl.acc.transport_ms;
+                }
+            }
+            ST(gpumcd_run(c, (int32_t)sid.size(), sid.data(), sn.data(), stream));
+            for (int t = 0; t < 2; ++t)
+                if (probe[t] >= 0) {
+                    transport_ms += c->plans.at(probe[t]).acc.transport_ms - before[t];
+                    ++sequences;
+                }
+        }
         ++rounds;
         for (size_t r = 0, i = 0; r < rid.size(); ++r) {
             while (ids[i] != rid[r]) ++i;
@@ -1242,6 +1296,7 @@ gpumcd_status gpumcd_run_to_uncertainty(gpumcd_ctx *c, int32_t n_plans, const in
     }
     if (rounds_out) *rounds_out = rounds;
     if (transport_ms_out) *transport_ms_out = transport_ms;
+    if (sequences_out) *sequences_out = sequences;
     return GPUMCD_OK;
 }
 

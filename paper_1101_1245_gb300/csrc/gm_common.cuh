@@ -108,8 +108,8 @@ struct __align__(16) PlanDev {
     int32_t src_type, beam;
     uint32_t e_src_q, n_phsp;     // n_phsp: phase-space records (spec holds them)
     unsigned long long hist_base;  // first history of this launch
-    unsigned long long n_hist;     // histories in this launch
-    uint32_t e_group, pad_g;       // e_group: spectrum stratified over aligned blocks of 2^16 histories
+    const uint32_t *order;         // e_group: the launch's histories in claim order (offsets from hist_base)
+    uint32_t e_group, n_sorted;    // e_group: a spectrum grouped by energy; n_sorted: histories `order` covers
 };
 static_assert(sizeof(PlanDev) == 160, "the plan table in shared memory keeps its size");
 

@@ -354,8 +354,9 @@ __device__ __forceinline__ float sample_spectrum(const PlanDev &P, float z) {
 // Primary of history h of plan P (§II.C.2 initParticle): pencil or square
 // parallel beam entering through z = 0 along +z; with PHSP, a phase-space
 // plan's primary is record h mod n as listed (the first draw is still taken,
-// so the draw counter starts where the beams' does), and a grouped spectrum
-// is sampled stratified over aligned blocks of 2^16 histories.
+// so the draw counter starts where the beams' does).  A spectrum grouped by
+// energy draws its energies as an ungrouped one does: the grouping orders the
+// claims (refill), not the sample.
 template <bool PHSP>
 __device__ __forceinline__ uint32_t make_primary(Lane &p, const PlanDev &P, uint32_t plan, uint64_t h) {
     p.hist = (uint32_t)h;
@@ -388,20 +389,7 @@ __device__ __forceinline__ uint32_t make_primary(Lane &p, const PlanDev &P, uint
     p.ux = 0.0f;
     p.uy = 0.0f;
     p.uz = 1.0f;
-    float zq = u01(r.z);
-    if (PHSP && P.e_group) {
-        // energy grouping (§IV): history j of the aligned block k of 2^16 takes
-        // stratum (64 bitrev10(j / 64) + j mod 64 + r_k) mod 2^16, r_k the
-        // block's own draw (counter (0, 0, 0, k): lineage 0 belongs to no
-        // particle).  64 consecutive histories take consecutive strata, a block
-        // takes each stratum once, and over r_k every quantile is uniform, so
-        // the energy is unbiased for any history count and depends on h alone.
-        // The quantile (s + u) / 2^16 is exact to 2^-24, 1/256 of a stratum.
-        const uint32_t k = (uint32_t)(h >> 16), j = (uint32_t)h & 0xFFFFu;
-        const uint4 rb = philox4x32_10(make_uint4(0u, 0u, 0u, k), make_uint2(P.key_lo, P.key_hi));
-        const uint32_t st = ((__brev(j >> 6) >> 22) * 64u + (j & 63u) + (rb.x & 0xFFFFu)) & 0xFFFFu;
-        zq = fminf(((float)st + zq) * (1.0f / 65536.0f), 1.0f);
-    }
+    const float zq = u01(r.z);
     p.E = P.n_spec > 0 ? __float2uint_rn(sample_spectrum(P, zq) * kInvQf) : P.e_src_q;
     p.act = true;
     return p.E;
@@ -846,7 +834,11 @@ __device__ int refill(const TransportArgs &A, const Smem &S, CtaFlags &F, Lane &
             }
             const uint32_t plan = A.prim_plan[t][a];
             const PlanDev &P = S.plans[plan];
-            ledger_add(S, plan, 0, make_primary<PHSP>(p, P, plan, P.hist_base + (g - A.prim_off[t][a])));
+            unsigned long long j = g - A.prim_off[t][a];
+            // a spectrum grouped by energy: its histories are claimed in
+            // decreasing order of their energy (the order its launch sorted)
+            if (PHSP && P.e_group && j < P.n_sorted) j = __ldg(P.order + j);
+            ledger_add(S, plan, 0, make_primary<PHSP>(p, P, plan, P.hist_base + j));
             if (KERMA && t == 1) {
                 // photon-only mode: a primary electron deposits where it enters
                 if (inside(P, p.x, p.y, p.z)) {
@@ -1190,6 +1182,95 @@ cudaError_t launch_transport(const TransportArgs &a, int grid, int block, int bl
     if (!fn) return cudaErrorInvalidConfiguration;
     if (a.tab_bytes < tab_bytes(1) || a.tab_bytes > (uint32_t)TAB_BYTES) return cudaErrorInvalidValue;
     fn<<<grid, block, transport_smem_bytes(a.tab_bytes), s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Energy grouping of a spectrum (GPUMCD §IV): before a launch, a counting sort
+// puts the plan's histories in decreasing order of their energy's spectrum bin,
+// and the launch claims them in that order.  Each history draws its energy as
+// an ungrouped one does (the same draw of make_primary), so the tally does not
+// change; warps, and the whole grid at any moment, start histories of similar
+// energy, the longest first.
+// ---------------------------------------------------------------------------
+constexpr int GROUP_THREADS = 256;
+constexpr uint32_t GROUP_PER_BLOCK = 16 * GROUP_THREADS;
+
+// The spectrum bin of history h's energy, counted from the top.
+__device__ __forceinline__ int group_key(const PlanDev &P, unsigned long long h) {
+    Lane p;
+    p.hist = (uint32_t)h;
+    p.lin_lo = 1u;
+    p.lin_hi = 0u;
+    p.draw = 0u;
+    p.plan = 0u;
+    const uint4 r = draw4(p, P);
+    const float z = u01(r.z);
+    const float *cdf = P.spec;
+    int lo = 0, hi = P.n_spec - 1;  // first bin with cdf[i+1] >= z, as sample_spectrum finds it
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(cdf + mid + 1) >= z) hi = mid; else lo = mid + 1;
+    }
+    return P.n_spec - 1 - lo;
+}
+
+__global__ void __launch_bounds__(GROUP_THREADS) k_group_count(const __grid_constant__ PlanDev P, uint32_t n,
+                                                               unsigned *count) {
+    __shared__ unsigned local[GPUMCD_MAX_SPECTRUM_BINS];
+    for (int i = threadIdx.x; i < P.n_spec; i += blockDim.x) local[i] = 0u;
+    __syncthreads();
+    const uint32_t j0 = blockIdx.x * GROUP_PER_BLOCK;
+    for (uint32_t j = j0 + threadIdx.x; j < n && j < j0 + GROUP_PER_BLOCK; j += blockDim.x)
+        atomicAdd(&local[group_key(P, P.hist_base + j)], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < P.n_spec; i += blockDim.x)
+        if (local[i]) atomicAdd(&count[i], local[i]);
+}
+
+// Exclusive prefix sum of the bin counts, in place (one thread: at most 1024 bins).
+__global__ void k_group_scan(unsigned *count, int n_bins) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned s = 0;
+    for (int i = 0; i < n_bins; ++i) {
+        const unsigned c = count[i];
+        count[i] = s;
+        s += c;
+    }
+}
+
+// Each block reserves, per bin, room for its histories of that bin, then
+// writes their offsets there (the order within a bin is not fixed: claims in
+// any order give the same tally).
+__global__ void __launch_bounds__(GROUP_THREADS) k_group_scatter(const __grid_constant__ PlanDev P, uint32_t n,
+                                                                 unsigned *cursor, uint32_t *order) {
+    __shared__ unsigned local[GPUMCD_MAX_SPECTRUM_BINS];
+    __shared__ unsigned base[GPUMCD_MAX_SPECTRUM_BINS];
+    for (int i = threadIdx.x; i < P.n_spec; i += blockDim.x) local[i] = 0u;
+    __syncthreads();
+    const uint32_t j0 = blockIdx.x * GROUP_PER_BLOCK;
+    for (uint32_t j = j0 + threadIdx.x; j < n && j < j0 + GROUP_PER_BLOCK; j += blockDim.x)
+        atomicAdd(&local[group_key(P, P.hist_base + j)], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < P.n_spec; i += blockDim.x) {
+        base[i] = local[i] ? atomicAdd(&cursor[i], local[i]) : 0u;
+        local[i] = 0u;
+    }
+    __syncthreads();
+    for (uint32_t j = j0 + threadIdx.x; j < n && j < j0 + GROUP_PER_BLOCK; j += blockDim.x) {
+        const int k = group_key(P, P.hist_base + j);
+        order[base[k] + atomicAdd(&local[k], 1u)] = j;
+    }
+}
+
+cudaError_t launch_group_order(const PlanDev &P, uint32_t n, unsigned *count, uint32_t *order, cudaStream_t s) {
+    if (P.n_spec < 1 || P.n_spec > GPUMCD_MAX_SPECTRUM_BINS || n == 0) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(count, 0, (size_t)P.n_spec * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (n + GROUP_PER_BLOCK - 1) / GROUP_PER_BLOCK;
+    k_group_count<<<blocks, GROUP_THREADS, 0, s>>>(P, n, count);
+    k_group_scan<<<1, 32, 0, s>>>(count, P.n_spec);
+    k_group_scatter<<<blocks, GROUP_THREADS, 0, s>>>(P, n, count, order);
     return cudaGetLastError();
 }
 

@@ -269,84 +269,24 @@ def _strata_deviation(e, edges, w):
     return float(np.max(np.abs(counts - len(e) * cdf)))
 
 
-BLOCK = 65536  # histories per aligned block of a grouped spectrum
-
-
-def _strata(e, edges, w):
-    """The stratum (s with quantile in (s/B, (s+1)/B]) of each energy, by
-    inverting the spectrum's piecewise-linear CDF."""
-    cdf = np.concatenate([[0.0], np.cumsum(w) / np.sum(w)])
-    q = np.interp(e, edges, cdf)
-    return np.ceil(q * BLOCK).astype(np.int64) - 1
-
-
-def _grouped(n_bins=64):
-    edges, w = W.synthetic_6mv_spectrum(n_bins=n_bins)
-    src = W.Source(W.PHOTON, W.BEAM_PENCIL, center_cm=(1.0, 1.0), spectrum_edges=edges,
-                   spectrum_weights=w, energy_grouping=W.ENERGY_GROUPED)
-    return src, edges, w
-
-
-@pytest.mark.parametrize("block", [0, 3])
-def test_grouped_spectrum_block_takes_every_stratum_once(block):
-    """A grouped spectrum (§IV's grouping of similar energies) stratifies each
-    aligned block of 2^16 histories: its histories take the 2^16 equal-probability
-    strata of the cumulative spectrum once each.  Pinned by what that fixes: the
-    inverted quantiles of a whole block are a permutation of the strata, and for
-    every bin edge the count below it is n CDF(edge) to within one; iid draws
-    miss that bound by tens."""
-    src, edges, w = _grouped()
-    h0 = block * BLOCK
-    e = oracle.primary_energies(src, h0, h0 + BLOCK, seed=12)
-    assert e.min() >= edges[0] and e.max() <= edges[-1]
-    assert np.array_equal(np.sort(_strata(e, edges, w)), np.arange(BLOCK))
-    assert _strata_deviation(e, edges, w) <= 1.0 + 1e-9
-    src.energy_grouping = W.ENERGY_UNGROUPED
-    iid = oracle.primary_energies(src, h0, h0 + BLOCK, seed=12)
-    assert _strata_deviation(iid, edges, w) > 10.0
-
-
-def test_grouped_spectrum_chunks_take_consecutive_strata_in_bit_reversed_order():
-    """64 consecutive histories (an aligned chunk, two warps' claims) take 64
-    consecutive strata, so a warp starts histories of similar energy; the
-    chunks of a block follow the bit-reversed order of their index, shifted by
-    the block's rotation r: chunk c starts at stratum 64 bitrev10(c) + r."""
-    src, edges, w = _grouped()
-    s = _strata(oracle.primary_energies(src, BLOCK, 2 * BLOCK, seed=5), edges, w).reshape(1024, 64)
-    first = s[:, 0]
-    assert np.all((s - first[:, None]) % BLOCK == np.arange(64)[None, :])
-    rot = int(first[0])  # chunk 0 starts at the rotation
-    rev = np.array([int(f"{c:010b}"[::-1], 2) for c in range(1024)])
-    assert np.array_equal(first, (64 * rev + rot) % BLOCK)
-    # the rotation is the block's own draw: other blocks and seeds differ
-    s2 = _strata(oracle.primary_energies(src, 2 * BLOCK, 2 * BLOCK + 64, seed=5), edges, w)
-    s3 = _strata(oracle.primary_energies(src, BLOCK, BLOCK + 64, seed=6), edges, w)
-    assert s2[0] != rot and s3[0] != rot
-
-
-def test_grouped_spectrum_any_prefix_is_spread_and_unbiased():
-    """Any history count is unbiased: over the block's random rotation each
-    history's quantile is uniform on (0, 1].  Checked over 300 seeds on a
-    ragged prefix of 1000 histories (15 chunks and a part): the mean energy
-    matches the spectrum's mean within its standard error.  And a prefix of
-    16 chunks spreads evenly: one chunk in every sixteenth of the quantile
-    range, so the count below each 1/16 quantile is exact to one chunk."""
-    src, edges, w = _grouped()
-    mean = float(np.sum(w * 0.5 * (edges[:-1] + edges[1:])) / np.sum(w))
-    m = np.array([oracle.primary_energies(src, 0, 1000, seed=100 + k).mean() for k in range(300)])
-    assert abs(m.mean() - mean) <= 3.5 * m.std(ddof=1) / math.sqrt(len(m))
-    s = _strata(oracle.primary_energies(src, 7 * BLOCK, 7 * BLOCK + 1024, seed=9), edges, w)
-    counts = np.array([(s < q * BLOCK // 16).sum() for q in range(1, 16)])
-    assert np.all(np.abs(counts - 64 * np.arange(1, 16)) <= 64)
-
-
-def test_grouped_spectrum_depends_on_the_history_index_alone():
-    """The energy of history h depends on h and the seed only, so any split
-    of a plan's histories into runs (and any batching) draws the same energies;
-    a monoenergetic beam is unchanged."""
-    src, _, _ = _grouped(16)
-    whole = oracle.primary_energies(src, 0, 3 * BLOCK + 500, seed=3)
-    for a, b in ((0, 17), (17, 70_001), (70_001, 3 * BLOCK + 500), (BLOCK - 5, BLOCK + 5)):
-        assert np.array_equal(oracle.primary_energies(src, a, b, seed=3), whole[a:b])
+def test_grouped_spectrum_draws_what_an_ungrouped_one_draws():
+    """Energy grouping (§IV's grouping of similar energies) of a spectrum is a
+    schedule: the GPU claims a launch's histories in decreasing order of their
+    energy, and each history draws its energy as it would ungrouped.  So the
+    oracle's grouped and ungrouped spectra give the same energies and the same
+    tallies; a monoenergetic beam is unchanged."""
+    edges, w = W.synthetic_6mv_spectrum(n_bins=64)
+    grouped = W.Source(W.PHOTON, W.BEAM_PENCIL, center_cm=(1.0, 1.0), spectrum_edges=edges,
+                       spectrum_weights=w, energy_grouping=W.ENERGY_GROUPED)
+    plain = W.Source(W.PHOTON, W.BEAM_PENCIL, center_cm=(1.0, 1.0), spectrum_edges=edges,
+                     spectrum_weights=w)
+    a = oracle.primary_energies(grouped, 70_000, 72_000, seed=12)
+    b = oracle.primary_energies(plain, 70_000, 72_000, seed=12)
+    assert np.array_equal(a, b)
+    assert _strata_deviation(a, edges, w) > 3.0  # iid draws, not strata
+    ph = W.homogeneous((8, 8, 16), 0.5, W.MAT_WATER, 1.0)
+    ra = oracle.simulate(W.MATERIALS, P, ph, grouped, 500, 3)
+    rb = oracle.simulate(W.MATERIALS, P, ph, plain, 500, 3)
+    assert np.array_equal(ra.sum_e, rb.sum_e)
     mono = W.Source(W.PHOTON, W.BEAM_PENCIL, energy=2.0, energy_grouping=W.ENERGY_GROUPED)
     assert np.all(oracle.primary_energies(mono, 0, 50, seed=1) == 2.0)
