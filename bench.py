@@ -1009,12 +1009,15 @@ def run_grouping(args):
     (128^3 water), with the paper's timing history counts, each source
     ungrouped against grouped (energy_grouping):
     - a phase space of 1e6 records in random order (6 MV-like photons, 1-15
-      MeV electrons), used as listed or stably sorted by decreasing energy;
+      MeV electrons), used as listed or stably sorted by decreasing energy:
+      two different, equally valid samples of the same dose;
     - a 10x10 cm^2 field whose spectrum (the same energies) is sampled on the
-      device, iid or stratified over the run from the top down.
-    The two forms give different, equally valid samples of the same dose; the
-    line reports the share of voxels above 10% of the maximum where they agree
-    within 3 combined sigma."""
+      device, its histories claimed as numbered or in decreasing order of
+      energy: the same sample, so on the same kernel the same tally.
+    The ungrouped spectrum is also timed on the phase-space kernel that runs
+    the grouped one (a same-kernel comparison).  The line reports the share of
+    voxels above 10% of the maximum where the two forms agree within 3
+    combined sigma."""
     import numpy as np
     import torch
 
