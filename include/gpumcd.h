@@ -58,21 +58,18 @@ typedef int32_t gpumcd_status;
 /* Energy grouping of a polyenergetic source (gpumcd_source.energy_grouping):
  * particles of similar energy are started together, the divergence measure
  * §IV proposes for polyenergetic beams.  Warps claim primaries in chunks from
- * one cursor, so consecutive histories run side by side.  With
- * GPUMCD_ENERGY_GROUPED:
- * - a phase space's records are stably sorted by decreasing E at
- *   gpumcd_plan_open; history h takes record h mod n of the sorted list (ties
- *   keep their listed order);
- * - a spectrum keeps its sample: each history draws its energy as it would
- *   ungrouped (run on the same kernel, the tallies are equal bit for bit, and
- *   they do not depend on how the histories are split); but each launch first
- *   sorts its histories of the plan by energy (a counting sort over the
- *   spectrum's bins, of at most 2^28 histories a launch; the rest are claimed
- *   as numbered) and claims them in decreasing order, so the warps, and the
- *   whole grid at any moment, start histories of similar energy, the longest
- *   first;
- * - a monoenergetic beam is unchanged.
- * A launch holding a grouped spectral plan runs the phase-space kernel, with
+ * one cursor, so consecutive claims run side by side.  With
+ * GPUMCD_ENERGY_GROUPED a spectrum or a phase space keeps its sample: each
+ * history starts as it would ungrouped (the same energy draw, or the same
+ * record h mod n of the list as given), so on the same kernel the tallies are
+ * equal bit for bit, for any split of the histories into runs.  What changes
+ * is the order of the claims: each launch first sorts its histories of the
+ * plan by their primary's energy (a counting sort over the spectrum's bins,
+ * or over 64 bins an octave of a record's energy, of at most 2^28 histories a
+ * launch; the rest are claimed as numbered) and claims them in decreasing
+ * order.  So the warps, and the whole grid at any moment, start histories of
+ * similar energy, the longest first.  A monoenergetic beam is unchanged.  A
+ * launch holding a grouped spectral plan runs the phase-space kernel, with
  * its restrictions. */
 #define GPUMCD_ENERGY_UNGROUPED 0
 #define GPUMCD_ENERGY_GROUPED 1
@@ -131,7 +128,7 @@ typedef struct {
 
 /* Launch tuning; 0 in a field keeps the current value.  See gpumcd_set_launch. */
 typedef struct {
-    uint32_t block_threads;   /* threads per CTA (multiple of 32, <= 512) */
+    uint32_t block_threads;   /* threads per CTA (multiple of 32, <= 1024) */
     uint32_t blocks_per_sm;   /* resident CTAs per SM of the persistent grid */
     uint32_t stack_capacity;  /* per-warp particle stack entries per type */
     uint32_t switch_high;     /* a warp switches type when the other stack holds this many (= stack_capacity: never) */

@@ -190,9 +190,10 @@ def phantom(ph, keep: _Keep) -> PhantomC:
 
 
 def source(src, keep: _Keep) -> SourceC:
-    """The C source.  Energy grouping (§IV) changes the sample of a phase space
-    only (its records sorted by decreasing energy, below); a grouped spectrum
-    draws as an ungrouped one does."""
+    """The C source.  Energy grouping (§IV) changes no sample: a grouped
+    spectrum or phase space starts every history as an ungrouped one does (the
+    grouping orders which histories run together, and the oracle runs them one
+    after another), so the flag is not passed on."""
     s = SourceC()
     s.particle = src.particle
     s.beam = src.beam
@@ -208,13 +209,9 @@ def source(src, keep: _Keep) -> SourceC:
         s.spec_weights = w.ctypes.data_as(_DP)
     else:
         s.n_spec = 0
-    grouped = getattr(src, "energy_grouping", 0) == 1
     ps = getattr(src, "phase_space", None)
     if ps is not None:
         a = np.ascontiguousarray(ps, dtype=np.float64).reshape(-1, 7)
-        if grouped:
-            # records grouped by energy (§IV): decreasing E, ties in listed order
-            a = np.ascontiguousarray(a[np.argsort(-a[:, 6], kind="stable")])
         keep.refs.append(a)
         s.n_phsp = len(a)
         s.phsp = a.ctypes.data_as(_DP)

@@ -68,10 +68,10 @@ typedef struct {
     double cx, cy, field;
     int32_t n_phsp;      /* beam 2: records */
     const double *phsp;  /* beam 2: [n_phsp][7] x, y, z (cm), ux, uy, uz, E (MeV) */
-    /* Energy grouping (§IV) changes no sample here: a grouped spectrum draws
-     * its energies as an ungrouped one does (the GPU orders the claims of its
-     * histories by energy, which leaves each history's draws unchanged), and a
-     * grouped phase space is sorted by the caller. */
+    /* Energy grouping (§IV) changes no sample here: a grouped spectrum or
+     * phase space starts every history as an ungrouped one does (the GPU
+     * orders the claims of its histories by energy, which leaves each
+     * history's primary and draws unchanged), so the source has no flag. */
 } om_source;
 
 typedef struct {

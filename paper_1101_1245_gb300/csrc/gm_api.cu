@@ -36,7 +36,7 @@ struct Plan {
     double energy, cx, cy, field;
     int32_t n_spec;
     uint32_t n_phsp = 0;     // phase-space records (held in `spec`)
-    bool e_group = false;    // a spectrum grouped by energy: claimed highest energies first
+    bool e_group = false;    // a spectrum or phase space grouped by energy: claimed highest energies first
     uint64_t seed;
     uint32_t W;
     uint64_t hist_sub = 0;   // histories handed to launch sequences (numbering of the next run)
@@ -65,7 +65,7 @@ struct Control {
 // gpumcd_submit on their own streams, so sequences can overlap on the device.
 struct Slot {
     DevBuf stacks, hard, queue[2][NT], control, plandev;
-    DevBuf order, gcount;  // claim orders of grouped spectra, and their sort's bin counts
+    DevBuf order, gcount;  // claim orders of grouped sources, and their sort's bin counts
     Control *h_control = nullptr;  // pinned: the control block after each launch
     PlanDev *h_plandev = nullptr;  // pinned: the sequence's plan table
     cudaStream_t own = nullptr;    // the slot's stream (asynchronous slots)
@@ -528,7 +528,7 @@ gpumcd_status gpumcd_plan_open(gpumcd_ctx *c, int32_t phantom_id, const gpumcd_s
     p.cy = src->center_cm[1];
     p.field = src->field_cm;
     p.n_spec = src->n_spectrum;
-    p.e_group = src->beam != GPUMCD_BEAM_PHASE_SPACE && src->n_spectrum > 0 &&
+    p.e_group = (src->beam == GPUMCD_BEAM_PHASE_SPACE || src->n_spectrum > 0) &&
                 src->energy_grouping == GPUMCD_ENERGY_GROUPED;
     p.seed = seed;
     p.W = n_batches;
@@ -552,8 +552,8 @@ gpumcd_status gpumcd_plan_open(gpumcd_ctx *c, int32_t phantom_id, const gpumcd_s
     }
     dev_free(c, tmp);
     if (st == GPUMCD_OK && p.beam == GPUMCD_BEAM_PHASE_SPACE) {
-        // records as float4 pairs (x, y, z, E) (ux, uy, uz, 0), direction normalised;
-        // all are checked before the optional stable sort by energy
+        // records as float4 pairs (x, y, z, E) (ux, uy, uz, 0), direction normalised,
+        // in the listed order (energy grouping orders a launch's claims, not the list)
         const int32_t n = src->n_phase_space;
         for (int32_t i = 0; i < n; ++i) {
             const double *r = src->phase_space + 7 * (size_t)i;
@@ -565,15 +565,9 @@ gpumcd_status gpumcd_plan_open(gpumcd_ctx *c, int32_t phantom_id, const gpumcd_s
                 break;
             }
         }
-        std::vector<int32_t> order((size_t)n);
-        std::iota(order.begin(), order.end(), 0);
-        if (st == GPUMCD_OK && src->energy_grouping == GPUMCD_ENERGY_GROUPED)
-            std::stable_sort(order.begin(), order.end(), [src](int32_t i, int32_t j) {
-                return src->phase_space[7 * (size_t)i + 6] > src->phase_space[7 * (size_t)j + 6];
-            });
         std::vector<float> h((size_t)n * 8);
         for (int32_t i = 0; i < n && st == GPUMCD_OK; ++i) {
-            const double *r = src->phase_space + 7 * (size_t)order[i];
+            const double *r = src->phase_space + 7 * (size_t)i;
             const double nu = std::sqrt(r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
             float *o = h.data() + 8 * (size_t)i;
             o[0] = (float)r[0], o[1] = (float)r[1], o[2] = (float)r[2], o[3] = (float)r[6];
@@ -804,7 +798,7 @@ void seq_close(gpumcd_ctx *c, Slot &sl, gpumcd_status result, float ms) {
 }
 
 // Validate a run request and enqueue its first launch on stream s.
-// Histories of a grouped spectrum a launch sorts by energy at most (2^28, a
+// Histories of a grouped source a launch sorts by energy at most (2^28, a
 // 1 GB claim order); the rest of a larger run is claimed as numbered.
 constexpr uint64_t kGroupSortMax = 1ull << 28;
 
@@ -895,7 +889,7 @@ gpumcd_status seq_start(gpumcd_ctx *c, Slot &sl, int32_t n_plans, const int32_t 
     A.counters = dc->counters;
     A.error = &dc->error;
 
-    // spectra grouped by energy: sort each one's histories of this launch by
+    // sources grouped by energy: sort each one's histories of this launch by
     // energy, on the sequence's stream ahead of the launch
     size_t n_order = 0;
     for (int i = 0; i < n_plans; ++i) n_order += sl.h_plandev[i].e_group ? sl.h_plandev[i].n_sorted : 0u;

@@ -109,7 +109,7 @@ struct __align__(16) PlanDev {
     uint32_t e_src_q, n_phsp;     // n_phsp: phase-space records (spec holds them)
     unsigned long long hist_base;  // first history of this launch
     const uint32_t *order;         // e_group: the launch's histories in claim order (offsets from hist_base)
-    uint32_t e_group, n_sorted;    // e_group: a spectrum grouped by energy; n_sorted: histories `order` covers
+    uint32_t e_group, n_sorted;    // e_group: a source grouped by energy; n_sorted: histories `order` covers
 };
 static_assert(sizeof(PlanDev) == 160, "the plan table in shared memory keeps its size");
 

@@ -354,8 +354,8 @@ __device__ __forceinline__ float sample_spectrum(const PlanDev &P, float z) {
 // Primary of history h of plan P (§II.C.2 initParticle): pencil or square
 // parallel beam entering through z = 0 along +z; with PHSP, a phase-space
 // plan's primary is record h mod n as listed (the first draw is still taken,
-// so the draw counter starts where the beams' does).  A spectrum grouped by
-// energy draws its energies as an ungrouped one does: the grouping orders the
+// so the draw counter starts where the beams' does).  A source grouped by
+// energy starts each history as an ungrouped one does: the grouping orders the
 // claims (refill), not the sample.
 template <bool PHSP>
 __device__ __forceinline__ uint32_t make_primary(Lane &p, const PlanDev &P, uint32_t plan, uint64_t h) {
@@ -835,7 +835,7 @@ __device__ int refill(const TransportArgs &A, const Smem &S, CtaFlags &F, Lane &
             const uint32_t plan = A.prim_plan[t][a];
             const PlanDev &P = S.plans[plan];
             unsigned long long j = g - A.prim_off[t][a];
-            // a spectrum grouped by energy: its histories are claimed in
+            // a source grouped by energy: its histories are claimed in
             // decreasing order of their energy (the order its launch sorted)
             if (PHSP && P.e_group && j < P.n_sorted) j = __ldg(P.order + j);
             ledger_add(S, plan, 0, make_primary<PHSP>(p, P, plan, P.hist_base + j));
@@ -1186,18 +1186,35 @@ cudaError_t launch_transport(const TransportArgs &a, int grid, int block, int bl
 }
 
 // ---------------------------------------------------------------------------
-// Energy grouping of a spectrum (GPUMCD §IV): before a launch, a counting sort
-// puts the plan's histories in decreasing order of their energy's spectrum bin,
-// and the launch claims them in that order.  Each history draws its energy as
-// an ungrouped one does (the same draw of make_primary), so the tally does not
-// change; warps, and the whole grid at any moment, start histories of similar
-// energy, the longest first.
+// Energy grouping of a spectrum or a phase space (GPUMCD §IV): before a
+// launch, a counting sort puts the plan's histories in decreasing order of
+// their primary's energy bin, and the launch claims them in that order.  Each
+// history starts as an ungrouped one does (the same draw, or the same record,
+// in make_primary), so the tally does not change; warps, and the whole grid at
+// any moment, start histories of similar energy, the longest first.
 // ---------------------------------------------------------------------------
 constexpr int GROUP_THREADS = 256;
 constexpr uint32_t GROUP_PER_BLOCK = 16 * GROUP_THREADS;
 
-// The spectrum bin of history h's energy, counted from the top.
+// Energy bins of a grouped phase space: 64 to an octave over [2^-10, 2^6) MeV,
+// from the float's exponent and top six mantissa bits (exact and monotone for
+// E > 0; energies outside the range share the end bins).
+constexpr int PHSP_GROUP_BINS = GPUMCD_MAX_SPECTRUM_BINS;
+static_assert(PHSP_GROUP_BINS == 1024, "16 octaves x 64 bins");
+
+__device__ __forceinline__ int group_bins(const PlanDev &P) {
+    return P.beam == GPUMCD_BEAM_PHASE_SPACE ? PHSP_GROUP_BINS : P.n_spec;
+}
+
+// The energy bin of history h's primary, counted from the top: a phase
+// space's record h mod n, or the spectrum bin the history's own draw picks.
 __device__ __forceinline__ int group_key(const PlanDev &P, unsigned long long h) {
+    if (P.beam == GPUMCD_BEAM_PHASE_SPACE) {
+        const float4 *ps = reinterpret_cast<const float4 *>(P.spec);
+        const float E = __ldg(ps + 2 * (size_t)(h % (unsigned long long)P.n_phsp)).w;
+        const int b = (int)(__float_as_uint(E) >> 17) - ((127 - 10) << 6);
+        return PHSP_GROUP_BINS - 1 - min(max(b, 0), PHSP_GROUP_BINS - 1);
+    }
     Lane p;
     p.hist = (uint32_t)h;
     p.lin_lo = 1u;
@@ -1218,13 +1235,14 @@ __device__ __forceinline__ int group_key(const PlanDev &P, unsigned long long h)
 __global__ void __launch_bounds__(GROUP_THREADS) k_group_count(const __grid_constant__ PlanDev P, uint32_t n,
                                                                unsigned *count) {
     __shared__ unsigned local[GPUMCD_MAX_SPECTRUM_BINS];
-    for (int i = threadIdx.x; i < P.n_spec; i += blockDim.x) local[i] = 0u;
+    const int nb = group_bins(P);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) local[i] = 0u;
     __syncthreads();
     const uint32_t j0 = blockIdx.x * GROUP_PER_BLOCK;
     for (uint32_t j = j0 + threadIdx.x; j < n && j < j0 + GROUP_PER_BLOCK; j += blockDim.x)
         atomicAdd(&local[group_key(P, P.hist_base + j)], 1u);
     __syncthreads();
-    for (int i = threadIdx.x; i < P.n_spec; i += blockDim.x)
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
         if (local[i]) atomicAdd(&count[i], local[i]);
 }
 
@@ -1246,13 +1264,14 @@ __global__ void __launch_bounds__(GROUP_THREADS) k_group_scatter(const __grid_co
                                                                  unsigned *cursor, uint32_t *order) {
     __shared__ unsigned local[GPUMCD_MAX_SPECTRUM_BINS];
     __shared__ unsigned base[GPUMCD_MAX_SPECTRUM_BINS];
-    for (int i = threadIdx.x; i < P.n_spec; i += blockDim.x) local[i] = 0u;
+    const int nb = group_bins(P);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) local[i] = 0u;
     __syncthreads();
     const uint32_t j0 = blockIdx.x * GROUP_PER_BLOCK;
     for (uint32_t j = j0 + threadIdx.x; j < n && j < j0 + GROUP_PER_BLOCK; j += blockDim.x)
         atomicAdd(&local[group_key(P, P.hist_base + j)], 1u);
     __syncthreads();
-    for (int i = threadIdx.x; i < P.n_spec; i += blockDim.x) {
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
         base[i] = local[i] ? atomicAdd(&cursor[i], local[i]) : 0u;
         local[i] = 0u;
     }
@@ -1264,12 +1283,13 @@ __global__ void __launch_bounds__(GROUP_THREADS) k_group_scatter(const __grid_co
 }
 
 cudaError_t launch_group_order(const PlanDev &P, uint32_t n, unsigned *count, uint32_t *order, cudaStream_t s) {
-    if (P.n_spec < 1 || P.n_spec > GPUMCD_MAX_SPECTRUM_BINS || n == 0) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(count, 0, (size_t)P.n_spec * sizeof(unsigned), s);
+    const int nb = P.beam == GPUMCD_BEAM_PHASE_SPACE ? (P.n_phsp > 0 ? PHSP_GROUP_BINS : 0) : P.n_spec;
+    if (nb < 1 || nb > GPUMCD_MAX_SPECTRUM_BINS || n == 0 || !P.spec) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(count, 0, (size_t)nb * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (n + GROUP_PER_BLOCK - 1) / GROUP_PER_BLOCK;
     k_group_count<<<blocks, GROUP_THREADS, 0, s>>>(P, n, count);
-    k_group_scan<<<1, 32, 0, s>>>(count, P.n_spec);
+    k_group_scan<<<1, 32, 0, s>>>(count, nb);
     k_group_scatter<<<blocks, GROUP_THREADS, 0, s>>>(P, n, count, order);
     return cudaGetLastError();
 }

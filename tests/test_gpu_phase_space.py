@@ -109,30 +109,35 @@ def _tied_phase_space(ph, n, seed):
     return src
 
 
-def test_grouped_by_energy_equals_the_sorted_list(ctx):
-    """GPUMCD_ENERGY_GROUPED is the listed records stably sorted by decreasing
-    energy: the tally, the ledger and every counter equal, bit for bit, those
-    of the same records sorted on the host (numpy's stable sort) and used as
-    listed.  997 records and 30,011 histories: a ragged last cycle."""
+def test_grouped_phase_space_equals_ungrouped(ctx):
+    """GPUMCD_ENERGY_GROUPED on a phase space orders each launch's claims by
+    the records' energies and leaves the sample alone: history h starts as
+    record h mod n of the list as given.  The tally, the ledger and every
+    counter equal, bit for bit, those of the ungrouped plan (997 records with
+    7 distinct energies in random order), split into ragged runs or not, and
+    also for fewer histories than records, where a list sorted by energy would
+    start only the highest-energy records."""
     ph = W.homogeneous((24, 24, 30), 0.5, W.MAT_WATER, 1.0)
     src = _tied_phase_space(ph, 997, 41)
     grouped = W.Source(W.PHOTON, W.BEAM_PHASE_SPACE, phase_space=src.phase_space,
                        energy_grouping=W.ENERGY_GROUPED)
-    k = np.argsort(-src.phase_space[:, 6], kind="stable")
-    listed = W.Source(W.PHOTON, W.BEAM_PHASE_SPACE, phase_space=src.phase_space[k].copy())
-    a = run_gpu(ctx, W.Plan("grouped", ph, grouped, 30_011, 9))
-    b = run_gpu(ctx, W.Plan("sorted", ph, listed, 30_011, 9))
-    assert np.array_equal(a.dose.view(np.uint64), b.dose.view(np.uint64))
-    assert np.array_equal(a.sigma.view(np.uint64), b.sigma.view(np.uint64))
-    for key in ("e_incident", "e_deposited", "e_escaped", "e_rest", "n_photon_real", "n_electron_steps"):
-        assert a.stats[key] == b.stats[key], key
-    assert a.stats["e_incident"] == _incident_quanta(listed, 30_011)
+    for runs in ([30_011], [10_007, 20_004], [300]):
+        n = sum(runs)
+        a = _phsp_kernel_runs(ctx, ph, grouped, 9, runs)
+        b = _phsp_kernel_runs(ctx, ph, src, 9, [n])
+        assert np.array_equal(a[0].view(np.uint64), b[0].view(np.uint64)), runs
+        assert np.array_equal(a[1].view(np.uint64), b[1].view(np.uint64)), runs
+        for key in ("e_incident", "e_deposited", "e_escaped", "e_rest", "n_photon_real", "n_electron_steps",
+                    "n_compton", "n_photo", "n_pair", "n_moller", "n_brem"):
+            assert a[2][key] == b[2][key], (runs, key)
+        assert a[2]["e_incident"] == _incident_quanta(src, n)
+        assert ledger_exact(a[2])
 
 
 def test_grouped_by_energy_parity(ctx):
-    """A grouped polyenergetic photon phase space against the oracle, which
-    applies the same order with its own sort: the parity bar of the other
-    phase-space tests."""
+    """A grouped polyenergetic photon phase space against the oracle (for
+    which grouping changes nothing): the parity bar of the other phase-space
+    tests."""
     ph = W.z_slabs((32, 32, 48), 0.5, [(3.0, W.MAT_WATER, 1.0), (2.0, W.MAT_BONE, 1.85),
                                        (6.0, W.MAT_LUNG, 0.26), (1e9, W.MAT_WATER, 1.0)])
     src = W.polyenergetic_phase_space(W.PHOTON, ph, 1009, seed=23)
@@ -141,9 +146,7 @@ def test_grouped_by_energy_parity(ctx):
     gpu = run_gpu(ctx, plan)
     ora = run_oracle(plan)
     assert ledger_exact(gpu.stats)
-    k = np.argsort(-src.phase_space[:, 6], kind="stable")
-    assert gpu.stats["e_incident"] == _incident_quanta(W.Source(W.PHOTON, W.BEAM_PHASE_SPACE,
-                                                                phase_space=src.phase_space[k]), 100_000)
+    assert gpu.stats["e_incident"] == _incident_quanta(src, 100_000)
     do, so = ora.dose_gy(ph), ora.sigma_gy(ph)
     mask = do > 0.1 * do.max()
     assert mask.sum() > 100
@@ -160,7 +163,7 @@ def test_energy_grouping_is_validated(ctx):
             ctx.plan_open(pid, W.Source(W.PHOTON, W.BEAM_PHASE_SPACE, phase_space=rec, energy_grouping=2), 1, 16)
         assert e.value.status == g.ERR_INVALID_ARG
         bad = np.array([[1.0, 1.0, 0.0, 0.0, 0.0, 1.0, 2.0], [1.0, 1.0, 0.0, 0.0, 0.0, 1.0, np.nan]])
-        with pytest.raises(g.GpumcdError) as e:  # checked before the sort
+        with pytest.raises(g.GpumcdError) as e:  # a record that is not finite
             ctx.plan_open(pid, W.Source(W.PHOTON, W.BEAM_PHASE_SPACE, phase_space=bad,
                                         energy_grouping=W.ENERGY_GROUPED), 1, 16)
         assert e.value.status == g.ERR_INVALID_ARG
@@ -173,21 +176,26 @@ def _mean_energy(edges, w):
 
 
 def _phsp_kernel_runs(ctx, ph, src, seed, runs):
-    """A plan run as `runs` on the phase-space kernel: beside it, in each launch,
-    a one-record phase space of the same particle type runs one history.
+    """A plan run as `runs` on the phase-space kernel: a phase space runs there
+    by itself; beside any other source, in each launch, a one-record phase
+    space of the same particle type runs one history (the launch's event
+    counters, which go to its first plan, then include that history).
     Returns the plan's dose, sigma and stats."""
     import torch
     pid = ctx.create_phantom(ph)
-    rec = np.array([[0.5 * ph.extent_cm[0], 0.5 * ph.extent_cm[1], 0.0, 0.0, 0.0, 1.0, 1.0]])
-    dummy = ctx.plan_open(pid, W.Source(src.particle, W.BEAM_PHASE_SPACE, phase_space=rec), 1, 8)
+    dummy = None
+    if src.beam != W.BEAM_PHASE_SPACE:
+        rec = np.array([[0.5 * ph.extent_cm[0], 0.5 * ph.extent_cm[1], 0.0, 0.0, 0.0, 1.0, 1.0]])
+        dummy = ctx.plan_open(pid, W.Source(src.particle, W.BEAM_PHASE_SPACE, phase_space=rec), 1, 8)
     plan = ctx.plan_open(pid, src, seed, 16)
     for n in runs:
-        ctx.run([plan, dummy], [n, 1])
+        ctx.run([plan] if dummy is None else [plan, dummy], [n] if dummy is None else [n, 1])
     d = torch.zeros(ph.nvox, dtype=torch.float64, device="cuda")
     s = torch.zeros_like(d)
     st = ctx.plan_result(plan, 0.5, d.data_ptr(), s.data_ptr())
     ctx.plan_close(plan)
-    ctx.plan_close(dummy)
+    if dummy is not None:
+        ctx.plan_close(dummy)
     ctx.destroy_phantom(pid)
     return d.cpu().numpy(), s.cpu().numpy(), st
 

@@ -1,5 +1,5 @@
 """Scheduling independence: the dose tally is bit-identical whatever the launch
-shape, the history split (energy-grouped spectra included), the
+shape, the history split (energy-grouped spectra and phase spaces included), the
 warp-aggregation mode or the overflow path,
 because each particle's random stream depends only on (seed, history,
 lineage, draw) and energies are integers."""
@@ -43,15 +43,19 @@ _EDGES, _W = W.synthetic_6mv_spectrum(n_bins=64)
 SOURCES = {
     "electron": W.Source(W.ELECTRON, W.BEAM_SQUARE, energy=12.0, center_cm=(6.0, 5.0), field_cm=4.0),
     "photon": W.Source(W.PHOTON, W.BEAM_SQUARE, energy=15.0, center_cm=(6.0, 5.0), field_cm=4.0),
-    # a spectrum grouped by energy (§IV): its strata follow from the history index
+    # a spectrum and a phase space grouped by energy (§IV): each launch claims
+    # its histories in decreasing order of energy, each history unchanged
     "grouped": W.Source(W.PHOTON, W.BEAM_SQUARE, center_cm=(6.0, 5.0), field_cm=4.0,
                         spectrum_edges=_EDGES, spectrum_weights=_W, energy_grouping=W.ENERGY_GROUPED),
+    "grouped_phsp": W.Source(W.ELECTRON, W.BEAM_PHASE_SPACE,
+                             phase_space=W.polyenergetic_phase_space(W.ELECTRON, _plan(), 1013, seed=7).phase_space,
+                             energy_grouping=W.ENERGY_GROUPED),
 }
 
 
 def _phsp_kernel_accepts(launch) -> bool:
-    """A grouped spectrum runs the phase-space kernel: no profile or
-    aggregation flag, refill at every pass."""
+    """Grouped sources run the phase-space kernel: no profile or aggregation
+    flag, refill at every pass."""
     return (launch.get("refill_period", 1) == 1
             and not launch.get("flags", 0) & (g.LAUNCH_WARP_AGGREGATE | g.LAUNCH_PROFILE))
 
@@ -65,7 +69,7 @@ def reference():
     return ph, out
 
 
-@pytest.mark.parametrize("kind", ["electron", "photon", "grouped"])
+@pytest.mark.parametrize("kind", ["electron", "photon", "grouped", "grouped_phsp"])
 @pytest.mark.parametrize("launch", [
     dict(),
     dict(block_threads=512, blocks_per_sm=2),
@@ -83,7 +87,7 @@ def reference():
     dict(refill_period=g.REFILL_WHEN_EMPTY),
 ])
 def test_bit_identical_across_launch_shapes(reference, kind, launch):
-    if kind == "grouped" and not _phsp_kernel_accepts(launch):
+    if kind.startswith("grouped") and not _phsp_kernel_accepts(launch):
         pytest.skip("outside the phase-space kernel's launch restrictions")
     ph, out = reference
     ctx = make_ctx(**launch)
@@ -100,11 +104,12 @@ def test_bit_identical_across_launch_shapes(reference, kind, launch):
     assert st["n_moller"] + st["n_brem"] == st["n_hard_real"]
 
 
-@pytest.mark.parametrize("kind", ["electron", "photon", "grouped"])
+@pytest.mark.parametrize("kind", ["electron", "photon", "grouped", "grouped_phsp"])
 @pytest.mark.parametrize("flags", [0, g.LAUNCH_GRAPH])
 def test_split_runs_equal_one_run(reference, kind, flags):
-    """Also replays one captured graph with new kernel arguments per run.  A
-    grouped spectrum included: its strata depend on the history index alone."""
+    """Also replays one captured graph with new kernel arguments per run.
+    Grouped sources included: each run sorts its own histories' claims, and
+    no history's primary depends on that order."""
     ph, out = reference
     ctx = make_ctx(flags=flags)
     d, s, st = _dose(ctx, ph, SOURCES[kind], 40_000, 99, splits=(10_000, 17_000, 13_000))

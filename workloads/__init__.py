@@ -152,8 +152,10 @@ class Source:
     # BEAM_PHASE_SPACE: records (n, 7) = x, y, z (cm), ux, uy, uz, E (MeV), all of
     # `particle`; history h starts as record h mod n
     phase_space: Optional[np.ndarray] = None
-    # ENERGY_GROUPED: the records are used stably sorted by decreasing E, so
-    # that consecutive histories start at nearby energies (§IV)
+    # ENERGY_GROUPED (spectra and phase spaces): each launch claims its
+    # histories in decreasing order of their primary's energy, so that the
+    # histories started together have nearby energies (§IV); every history
+    # starts as it would ungrouped
     energy_grouping: int = ENERGY_UNGROUPED
 
     @property
