@@ -891,20 +891,29 @@ gpumcd_status seq_start(gpumcd_ctx *c, Slot &sl, int32_t n_plans, const int32_t 
 
     // sources grouped by energy: sort each one's histories of this launch by
     // energy, on the sequence's stream ahead of the launch
-    size_t n_order = 0;
-    for (int i = 0; i < n_plans; ++i) n_order += sl.h_plandev[i].e_group ? sl.h_plandev[i].n_sorted : 0u;
+    // (the orders of all grouped plans, then one plan's keys: the plans' sorts
+    // run one after another on the stream and share the key scratch)
+    size_t n_order = 0, n_keys = 0;
+    for (int i = 0; i < n_plans; ++i) {
+        const PlanDev &d = sl.h_plandev[i];
+        if (!d.e_group) continue;
+        n_order += d.n_sorted;
+        n_keys = std::max<size_t>(n_keys, d.n_sorted);
+    }
     if (n_order > 0) {
-        if (sl.order.bytes < n_order * 4) {
+        const size_t bytes = n_order * 4 + n_keys * 2;
+        if (sl.order.bytes < bytes) {
             dev_free(c, sl.order);  // the slot's last sequence has finished: nothing pending on it
-            ST(dev_alloc(c, sl.order, n_order * 4));
+            ST(dev_alloc(c, sl.order, bytes));
         }
         if (!sl.gcount.p) ST(dev_alloc(c, sl.gcount, GPUMCD_MAX_SPECTRUM_BINS * sizeof(unsigned)));
         uint32_t *ord = (uint32_t *)sl.order.p;
+        uint16_t *keys = (uint16_t *)((uint32_t *)sl.order.p + n_order);
         for (int i = 0; i < n_plans; ++i) {
             PlanDev &d = sl.h_plandev[i];
             if (!d.e_group) continue;
             d.order = ord;
-            CK(launch_group_order(d, d.n_sorted, (unsigned *)sl.gcount.p, ord, s));
+            CK(launch_group_order(d, d.n_sorted, (unsigned *)sl.gcount.p, keys, ord, s));
             ord += d.n_sorted;
         }
     }

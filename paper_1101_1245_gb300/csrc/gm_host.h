@@ -46,9 +46,10 @@ cudaError_t transport_configure();
 cudaError_t launch_transport(const TransportArgs &a, int grid, int block, int blocks_per_sm, cudaStream_t s);
 // Claim order of a spectrum or phase space grouped by energy: order[0..n) =
 // offsets j of the histories hist_base + j of plan P, in decreasing order of
-// their primary's energy bin; count holds GPUMCD_MAX_SPECTRUM_BINS unsigned of
-// scratch.
-cudaError_t launch_group_order(const PlanDev &P, uint32_t n, unsigned *count, uint32_t *order, cudaStream_t s);
+// their primary's energy bin; count (GPUMCD_MAX_SPECTRUM_BINS unsigned) and
+// keys (n uint16_t) are scratch.
+cudaError_t launch_group_order(const PlanDev &P, uint32_t n, unsigned *count, uint16_t *keys, uint32_t *order,
+                               cudaStream_t s);
 cudaError_t launch_debug_sample(const float *tab, const Phys &phys, int kind, float p0, int material,
                                 const float *spec, int n_spec, uint64_t n, uint64_t seed, float *out,
                                 cudaStream_t s);

@@ -399,11 +399,15 @@ __device__ __forceinline__ uint32_t make_primary(Lane &p, const PlanDev &P, uint
 // Photon transport
 // ---------------------------------------------------------------------------
 // Photon (GPUMCD §II.A).  photon_flight: one Woodcock flight; true when it
-// ends on a real event, with its voxel and the word that picks the
-// interaction.  photon_interact: that interaction (Compton, photoelectric or
-// pair, by the partial attenuation coefficients of the voxel's material).
-__device__ __forceinline__ bool photon_flight(const TransportArgs &A, const Smem &S, Lane &p, uint32_t &idx_out,
-                                              uint32_t &rz) {
+// ends on a real event, with its voxel, the word that picks the interaction,
+// and the voxel's material, density and attenuation coefficient.  xp (the
+// energy's grid coordinate) and mu_hat (the majorant) are the caller's, taken
+// once for all flights of a pass: the energy does not change on a fictitious
+// event.  photon_interact: that interaction (Compton, photoelectric or pair,
+// by the partial attenuation coefficients of the voxel's material).
+__device__ __forceinline__ bool photon_flight(const TransportArgs &A, const Smem &S, Lane &p, float xp,
+                                              float mu_hat, uint32_t &idx_out, uint32_t &rz, int &m_out,
+                                              float &rho_out, float &mu_out) {
     const PlanDev &P = S.plans[p.plan];
     const Phys &ph = A.phys;
     if (p.E < ph.p_cut_q) {
@@ -416,8 +420,6 @@ __device__ __forceinline__ bool photon_flight(const TransportArgs &A, const Smem
         p.act = false;
         return false;
     }
-    const float xp = fmaf(__log2f((float)p.E), ph.grid.ph_a, ph.grid.ph_bq);
-    const float mu_hat = interp_ldg(P.maj, xp);
     const uint4 r = draw4(p, P);
     const float s = -__logf(u01(r.x)) / mu_hat;
     p.x = fmaf(s, p.ux, p.x);
@@ -441,22 +443,20 @@ __device__ __forceinline__ bool photon_flight(const TransportArgs &A, const Smem
     count(S, CNT_PH_REAL);
     idx_out = idx;
     rz = r.z;
+    m_out = m;
+    rho_out = rho;
+    mu_out = mu;
     return true;
 }
 
 template <bool KERMA>
 __device__ __forceinline__ void photon_interact(const TransportArgs &A, const Smem &S, Lane &p, uint32_t idx,
-                                                uint32_t rz, int gw, int w) {
+                                                uint32_t rz, float xp, int m, float rho, float mu, int gw,
+                                                int w) {
     const PlanDev &P = S.plans[p.plan];
     const Phys &ph = A.phys;
-    const float xp = fmaf(__log2f((float)p.E), ph.grid.ph_a, ph.grid.ph_bq);
-    const uint32_t vw = __ldg(P.vox + idx);
-    const int m = vw & (NMAT - 1);
-    const float rho = (float)(vw >> 4) * kRhoQ;
     const float *tp = S.tab + tab_ph(m);
     const bool pair_open = p.E > ph.two_mc2_q;
-    float mu = rho * interp(tp, xp);
-    if (!pair_open) mu = rho * (interp(tp + G, xp) + interp(tp + 2 * G, xp));
     const float muC = rho * interp(tp + G, xp);
     const float mupe = rho * interp(tp + 2 * G, xp);
     const float q = u01(rz) * mu;
@@ -1088,17 +1088,23 @@ __global__ void __launch_bounds__(MAXT, MINB) k_transport(const __grid_constant_
             // real, then the real events' interactions together: with many
             // fictitious events (low densities under a high majorant) more
             // lanes reach an interaction per pass; in a homogeneous medium
-            // every first flight is real and the loop ends at once.
+            // every first flight is real and the loop ends at once.  The
+            // energy, so its grid coordinate and majorant, stays the same
+            // over the flights of a pass.
             uint32_t pidx = 0u, prz = 0u;
             bool real = false;
+            const float xp = fmaf(__log2f((float)p.E), A.phys.grid.ph_a, A.phys.grid.ph_bq);
+            const float mu_hat = p.act ? interp_ldg(S.plans[p.plan].maj, xp) : 1.0f;
+            int rm = 0;
+            float rrho = 0.f, rmu = 0.f;
             for (int k = 0; k < PH_FLIGHTS; ++k) {
                 const bool fly = p.act && !real;
                 const unsigned flym = __ballot_sync(FULL, fly);
                 if (flym == 0u) break;
                 if (lane == 0) atomicAdd(&S.cnt[CNT_PH_EVENTS], (unsigned long long)__popc(flym));
-                if (fly) real = photon_flight(A, S, p, pidx, prz);
+                if (fly) real = photon_flight(A, S, p, xp, mu_hat, pidx, prz, rm, rrho, rmu);
             }
-            if (real) photon_interact<KERMA>(A, S, p, pidx, prz, gw, w);
+            if (real) photon_interact<KERMA>(A, S, p, pidx, prz, xp, rm, rrho, rmu, gw, w);
         } else {
             uint32_t dep_idx = 0, dep_e = 0;
             bool stepped = false;
@@ -1232,15 +1238,28 @@ __device__ __forceinline__ int group_key(const PlanDev &P, unsigned long long h)
     return P.n_spec - 1 - lo;
 }
 
+// Count: each history's key, once, into keys[j]; the block's bin counts into
+// count.  Lanes of a warp with the same key add once (one shared atomic per
+// distinct key in the warp).
 __global__ void __launch_bounds__(GROUP_THREADS) k_group_count(const __grid_constant__ PlanDev P, uint32_t n,
-                                                               unsigned *count) {
+                                                               unsigned *count, uint16_t *keys) {
     __shared__ unsigned local[GPUMCD_MAX_SPECTRUM_BINS];
     const int nb = group_bins(P);
+    const unsigned lt = lanemask_lt();
+    // the block's histories in rounds of one per thread: the same trip count
+    // for every thread, so whole warps take part in each match
+    const uint32_t j0 = blockIdx.x * GROUP_PER_BLOCK, jend = min(n, j0 + GROUP_PER_BLOCK);
     for (int i = threadIdx.x; i < nb; i += blockDim.x) local[i] = 0u;
     __syncthreads();
-    const uint32_t j0 = blockIdx.x * GROUP_PER_BLOCK;
-    for (uint32_t j = j0 + threadIdx.x; j < n && j < j0 + GROUP_PER_BLOCK; j += blockDim.x)
-        atomicAdd(&local[group_key(P, P.hist_base + j)], 1u);
+    for (uint32_t jb = j0; jb < jend; jb += blockDim.x) {
+        const uint32_t j = jb + threadIdx.x;
+        const int k = j < jend ? group_key(P, P.hist_base + j) : -1;
+        const unsigned same = __match_any_sync(FULL, k);
+        if (k >= 0) {
+            keys[j] = (uint16_t)k;
+            if ((same & lt) == 0u) atomicAdd(&local[k], (unsigned)__popc(same));
+        }
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < nb; i += blockDim.x)
         if (local[i]) atomicAdd(&count[i], local[i]);
@@ -1259,38 +1278,52 @@ __global__ void k_group_scan(unsigned *count, int n_bins) {
 
 // Each block reserves, per bin, room for its histories of that bin, then
 // writes their offsets there (the order within a bin is not fixed: claims in
-// any order give the same tally).
+// any order give the same tally).  The keys come from k_group_count.
 __global__ void __launch_bounds__(GROUP_THREADS) k_group_scatter(const __grid_constant__ PlanDev P, uint32_t n,
-                                                                 unsigned *cursor, uint32_t *order) {
+                                                                 unsigned *cursor, const uint16_t *keys,
+                                                                 uint32_t *order) {
     __shared__ unsigned local[GPUMCD_MAX_SPECTRUM_BINS];
     __shared__ unsigned base[GPUMCD_MAX_SPECTRUM_BINS];
     const int nb = group_bins(P);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    const uint32_t j0 = blockIdx.x * GROUP_PER_BLOCK, jend = min(n, j0 + GROUP_PER_BLOCK);
     for (int i = threadIdx.x; i < nb; i += blockDim.x) local[i] = 0u;
     __syncthreads();
-    const uint32_t j0 = blockIdx.x * GROUP_PER_BLOCK;
-    for (uint32_t j = j0 + threadIdx.x; j < n && j < j0 + GROUP_PER_BLOCK; j += blockDim.x)
-        atomicAdd(&local[group_key(P, P.hist_base + j)], 1u);
+    for (uint32_t jb = j0; jb < jend; jb += blockDim.x) {
+        const uint32_t j = jb + threadIdx.x;
+        const int k = j < jend ? (int)keys[j] : -1;
+        const unsigned same = __match_any_sync(FULL, k);
+        if (k >= 0 && (same & lt) == 0u) atomicAdd(&local[k], (unsigned)__popc(same));
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
         base[i] = local[i] ? atomicAdd(&cursor[i], local[i]) : 0u;
         local[i] = 0u;
     }
     __syncthreads();
-    for (uint32_t j = j0 + threadIdx.x; j < n && j < j0 + GROUP_PER_BLOCK; j += blockDim.x) {
-        const int k = group_key(P, P.hist_base + j);
-        order[base[k] + atomicAdd(&local[k], 1u)] = j;
+    for (uint32_t jb = j0; jb < jend; jb += blockDim.x) {
+        const uint32_t j = jb + threadIdx.x;
+        const int k = j < jend ? (int)keys[j] : -1;
+        const unsigned same = __match_any_sync(FULL, k);
+        const int leader = __ffs(same) - 1;
+        unsigned slot = 0u;
+        if (k >= 0 && lane == leader) slot = atomicAdd(&local[k], (unsigned)__popc(same));
+        slot = __shfl_sync(FULL, slot, leader);
+        if (k >= 0) order[base[k] + slot + (unsigned)__popc(same & lt)] = j;
     }
 }
 
-cudaError_t launch_group_order(const PlanDev &P, uint32_t n, unsigned *count, uint32_t *order, cudaStream_t s) {
+cudaError_t launch_group_order(const PlanDev &P, uint32_t n, unsigned *count, uint16_t *keys, uint32_t *order,
+                               cudaStream_t s) {
     const int nb = P.beam == GPUMCD_BEAM_PHASE_SPACE ? (P.n_phsp > 0 ? PHSP_GROUP_BINS : 0) : P.n_spec;
     if (nb < 1 || nb > GPUMCD_MAX_SPECTRUM_BINS || n == 0 || !P.spec) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(count, 0, (size_t)nb * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (n + GROUP_PER_BLOCK - 1) / GROUP_PER_BLOCK;
-    k_group_count<<<blocks, GROUP_THREADS, 0, s>>>(P, n, count);
+    k_group_count<<<blocks, GROUP_THREADS, 0, s>>>(P, n, count, keys);
     k_group_scan<<<1, 32, 0, s>>>(count, nb);
-    k_group_scatter<<<blocks, GROUP_THREADS, 0, s>>>(P, n, count, order);
+    k_group_scatter<<<blocks, GROUP_THREADS, 0, s>>>(P, n, count, keys, order);
     return cudaGetLastError();
 }
 

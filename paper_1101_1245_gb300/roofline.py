@@ -59,10 +59,11 @@ def alu_roofline(events_e_beam: int, events_ph_beam: int, kernel_ms: float, sm_m
 INST_PER_EVENT_C4_E_SEQ: Optional[float] = 17.43
 INST_PER_EVENT_C4_PH_SEQ: Optional[float] = 17.65
 # DRAM bytes (read + write) per event of the same case on the current kernel (one
-# 1024-thread CTA per SM, tables packed per material): 1.927 GB over 259.66e6
-# events (electron sequence) and 1.888 GB over 128.58e6 (photon sequence)
-TRAFFIC_BYTES_PER_EVENT_C4_E_SEQ: Optional[float] = 7.42
-TRAFFIC_BYTES_PER_EVENT_C4_PH_SEQ: Optional[float] = 14.68
+# 1024-thread CTA per SM, tables packed per material, a photon's majorant taken once
+# per pass): 1.935 GB over 259.66e6 events (electron sequence) and 1.885 GB over
+# 128.58e6 (photon sequence)
+TRAFFIC_BYTES_PER_EVENT_C4_E_SEQ: Optional[float] = 7.45
+TRAFFIC_BYTES_PER_EVENT_C4_PH_SEQ: Optional[float] = 14.66
 
 
 def alu_roofline_c4(events_e_seq: int, events_ph_seq: int, kernel_ms: float, sm_mhz: Optional[float],
