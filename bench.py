@@ -16,8 +16,9 @@ step = all 64 plans to 1%.
   histories and, bit for bit, the same tallies);
 - served: a Poisson stream of 1000 requests from the same distribution on
   resident phantoms with continuous batching (serve.py), p50/p99 latency;
-- the paper's timing workload (1e6 e- + 4e6 photons, 15 MeV, 128^3 water) as a
-  sub-record.
+- the paper's timing workload (1e6 e- + 4e6 photons, 15 MeV, 128^3 water) and
+  the heterogeneous slab configuration (1e7 photons of a 6 MV-like spectrum on
+  256^3, ungrouped and grouped by energy, also run to 1%) as sub-records.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload c4|c2|batched|served|geoms|ablation|kerma|grouping]
@@ -52,6 +53,9 @@ W_C4 = 16                       # batch tallies per plan of the batched workload
 # degrees of freedom for sigma
 W_C2 = 16
 CAP_C4 = 400_000_000            # histories per plan at most
+# the slab configuration's s_0.5 is ~12% at its 1e7 histories (0.2 cm voxels):
+# 1% takes ~1.5e9
+CAP_C3 = 2_000_000_000
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -489,6 +493,71 @@ def c2_subrecord(ctx, stream, steps: int, warmup: int, rank: int) -> dict:
             "ledger_exact": all(x["e_deposited"] + x["e_escaped"] + x["e_rest"] == x["e_incident"] for x in last)}
 
 
+def c3_subrecord(ctx, stream, steps: int, warmup: int, rank: int) -> dict:
+    """The heterogeneous slab configuration (256^3 at 0.2 cm: water / bone /
+    lung / water slabs of 3 / 2 / 6 / rest cm, a 6 MV-like photon spectrum on a
+    10x10 cm^2 field), ungrouped and grouped by energy (the same histories and
+    bit-identical tallies): its own 1e7 histories from a zeroed tally to FP64
+    dose and sigma, then the same plan run from zero to s_0.5 <= 1%."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    pl = W.config3()
+    sh = stream.cuda_stream
+    pid = ctx.create_phantom(pl.phantom)
+    d = torch.empty(pl.phantom.nvox, dtype=torch.float64, device="cuda")
+    sg = torch.empty_like(d)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out, tallies = {}, {}
+    for label, grouping in (("ungrouped", W.ENERGY_UNGROUPED), ("grouped", W.ENERGY_GROUPED)):
+        pl.source.energy_grouping = grouping
+        plan = ctx.plan_open(pid, pl.source, pl.seed, W_C2)
+
+        def step(i):
+            ctx.plan_reset(plan, rank_seed(rank, i), sh)
+            ctx.run([plan], [pl.n_histories], sh)
+            return ctx.plan_result(plan, THRESHOLD, d.data_ptr(), sg.data_ptr(), sh)
+
+        for i in range(warmup):
+            step(-1 - i)
+        ms, st = [], None
+        for i in range(steps):
+            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                ev[0].record(stream)
+                st = step(i)
+                ev[1].record(stream)
+            torch.cuda.synchronize()
+            ms.append(ev[0].elapsed_time(ev[1]))
+        # to 1%: a first round of the configuration's count, then rounds by s ~ 1/sqrt(N)
+        ctx.plan_reset(plan, rank_seed(rank, 0), sh)
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            ev[0].record(stream)
+            r = ctx.run_to_uncertainty([plan], [pl.n_histories], [CAP_C3], TARGET, THRESHOLD, sh)
+            ctx.plan_result(plan, THRESHOLD, d.data_ptr(), sg.data_ptr(), sh)
+            ev[1].record(stream)
+        torch.cuda.synchronize()
+        ms1 = ev[0].elapsed_time(ev[1])
+        tallies[label] = d.cpu().numpy()
+        out[label] = {"value": pl.n_histories / (statistics.median(ms) / 1e3), "ms_per_step": statistics.median(ms),
+                      "transport_ms": st["transport_ms"], "s05": st["s_thr"],
+                      "ledger_exact": st["e_deposited"] + st["e_escaped"] + st["e_rest"] == st["e_incident"],
+                      "to_1pct": {"value": r["histories"][0] / (ms1 / 1e3), "ms": ms1,
+                                  "histories": r["histories"][0], "rounds": r["rounds"], "s05": r["s_thr"][0],
+                                  "transport_ms": r["transport_ms"]}}
+        ctx.plan_close(plan)
+    ctx.destroy_phantom(pid)
+    return {"workload": "c3_slabs256_6MV_photon_1e7", "metric": "histories/s (1e7 photons, 6 MV-like spectrum, "
+            "256^3 slabs, to FP64 dose + sigma; and from zero to s_0.5 <= 1%)", "steps": steps, **out,
+            "grouped_speedup": out["ungrouped"]["ms_per_step"] / out["grouped"]["ms_per_step"],
+            "grouped_speedup_to_1pct": out["ungrouped"]["to_1pct"]["ms"] / out["grouped"]["to_1pct"]["ms"],
+            "grouped_dose_equals_ungrouped": bool(np.array_equal(tallies["ungrouped"], tallies["grouped"]))}
+
+
 def run_c4(args):
     """The contract line: the batched workload's 64 plans, each to s_0.5 <= 1%."""
     import numpy as np
@@ -613,6 +682,7 @@ def run_c4(args):
     for p in plans:
         ctx.plan_close(p)
     c2 = c2_subrecord(ctx, stream, steps=5, warmup=2, rank=rank) if rank == 0 else None
+    c3 = c3_subrecord(ctx, stream, steps=5, warmup=2, rank=rank) if rank == 0 else None
 
     # end to end through the C ABI with host buffers: each step uploads the 64
     # phantoms from pinned host memory, runs them to 1% and reads dose and
@@ -691,6 +761,7 @@ def run_c4(args):
                       "first_round_only": first_round},
             "served": served,
             "c2": c2,
+            "c3": c3,
             "roofline": roof,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "host_memory": "pinned", "steps": len(e2e),

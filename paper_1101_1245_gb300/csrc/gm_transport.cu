@@ -1265,15 +1265,33 @@ __global__ void __launch_bounds__(GROUP_THREADS) k_group_count(const __grid_cons
         if (local[i]) atomicAdd(&count[i], local[i]);
 }
 
-// Exclusive prefix sum of the bin counts, in place (one thread: at most 1024 bins).
-__global__ void k_group_scan(unsigned *count, int n_bins) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    unsigned s = 0;
-    for (int i = 0; i < n_bins; ++i) {
-        const unsigned c = count[i];
-        count[i] = s;
-        s += c;
+// Exclusive prefix sum of the bin counts, in place: one block of
+// GPUMCD_MAX_SPECTRUM_BINS threads, a bin each (scans within the warps, then
+// over the warps' totals).
+constexpr int GROUP_SCAN_THREADS = GPUMCD_MAX_SPECTRUM_BINS;
+__global__ void __launch_bounds__(GROUP_SCAN_THREADS) k_group_scan(unsigned *count, int n_bins) {
+    __shared__ unsigned warp_sum[GROUP_SCAN_THREADS / 32];
+    const int i = threadIdx.x, lane = i & 31, wid = i >> 5;
+    const unsigned c = i < n_bins ? count[i] : 0u;
+    unsigned v = c;  // inclusive scan within the warp
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned u = __shfl_up_sync(FULL, v, d);
+        if (lane >= d) v += u;
     }
+    if (lane == 31) warp_sum[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned t = lane < GROUP_SCAN_THREADS / 32 ? warp_sum[lane] : 0u;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned u = __shfl_up_sync(FULL, t, d);
+            if (lane >= d) t += u;
+        }
+        if (lane < GROUP_SCAN_THREADS / 32) warp_sum[lane] = t;  // inclusive over the warps
+    }
+    __syncthreads();
+    if (i < n_bins) count[i] = v - c + (wid > 0 ? warp_sum[wid - 1] : 0u);
 }
 
 // Each block reserves, per bin, room for its histories of that bin, then
@@ -1322,7 +1340,7 @@ cudaError_t launch_group_order(const PlanDev &P, uint32_t n, unsigned *count, ui
     if (e != cudaSuccess) return e;
     const unsigned blocks = (n + GROUP_PER_BLOCK - 1) / GROUP_PER_BLOCK;
     k_group_count<<<blocks, GROUP_THREADS, 0, s>>>(P, n, count, keys);
-    k_group_scan<<<1, 32, 0, s>>>(count, nb);
+    k_group_scan<<<1, GROUP_SCAN_THREADS, 0, s>>>(count, nb);
     k_group_scatter<<<blocks, GROUP_THREADS, 0, s>>>(P, n, count, keys, order);
     return cudaGetLastError();
 }
