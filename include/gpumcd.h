@@ -425,7 +425,11 @@ gpumcd_status gpumcd_debug_counters(gpumcd_ctx *ctx, uint64_t *out, int32_t *cou
  * grid of max_m rho_max[m] * Sigma_hard,m (1/cm); rho_max holds
  * GPUMCD_MAX_MATERIALS entries (g/cm^3, 0 for materials absent from the
  * phantom), each the largest density of that material after quantisation to
- * 2^-24 g/cm^3.  Errors: GPUMCD_ERR_NOT_FOUND for an unknown phantom. */
+ * 2^-24 g/cm^3.  Photon flights sample with the photon majorant.  An electron
+ * step samples its hard distance with its own voxel's rho * Sigma_hard at the
+ * step's start energy, an exact majorant because the step stays in the voxel;
+ * the electron half here is the phantom-wide bound of §II.B.3, kept for
+ * diagnostics.  Errors: GPUMCD_ERR_NOT_FOUND for an unknown phantom. */
 gpumcd_status gpumcd_debug_majorants(gpumcd_ctx *ctx, int32_t phantom, float *majorants, float *rho_max);
 
 /* Philox4x32-10 on the device: for i < n, out[4i..4i+3] = Philox(counter

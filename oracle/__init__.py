@@ -25,6 +25,7 @@ MAX_EL = 16
 FLAG_KERMA = 1
 FLAG_FIRST_COLLISION = 2
 FLAG_NO_MS = 4
+FLAG_VOXEL_EMAJOR = 8  # the per-voxel electron Woodcock majorant (see oracle.h)
 
 MEV_PER_G_TO_GY = 1.602176634e-10
 

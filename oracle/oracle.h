@@ -89,6 +89,13 @@ typedef struct {
 #define OM_FLAG_KERMA 1u           /* electrons deposit their energy where they are created */
 #define OM_FLAG_FIRST_COLLISION 2u /* a photon's first real interaction ends it: the photon leaving it is escaped */
 #define OM_FLAG_NO_MS 4u           /* electrons are not deflected */
+/* The electron Woodcock majorant of a step is its own voxel's hard
+ * cross-section at the start energy, rho0 Sigma_m0(T0) (Sigma_m rises with T,
+ * and a step stays in its voxel), and the candidate is tested in that voxel;
+ * without the flag, §II.B.3's majorant over the whole phantom, tested at the
+ * end point.  Both are exact Woodcock schemes; they differ in how often a
+ * fictitious candidate splits a step. */
+#define OM_FLAG_VOXEL_EMAJOR 8u
 
 /* ---- cross-sections and stopping powers (all mass quantities, cm^2/g or MeV cm^2/g) ---- */
 double om_sigma_kn(double k);                              /* per electron, cm^2; k = E/mc^2 */

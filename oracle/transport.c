@@ -566,7 +566,8 @@ static void transport_electron(ctx_t *c, part_t *p) {
         double L0 = rho0 * (om_l_col(mat0, T, P->t_c) + om_l_rad(mat0, T, P->k_c));
         double smax = P->estepe * T / L0;
         double dvox = distance_to_voxel_exit(c, p->x, p->u);
-        double sig_hat = electron_majorant(c, T);
+        double sig_hat = (c->flags & OM_FLAG_VOXEL_EMAJOR) ? rho0 * hard_sigma(c, m0, T) * 1.002
+                                                           : electron_majorant(c, T);
         double ehard = sig_hat > 0.0 ? -log(uniform(&s)) / sig_hat : INFINITY;
         /* e_s = min{d_vox, e_s-max, e_hard} */
         double es = dvox < smax ? dvox : smax;
@@ -611,9 +612,10 @@ static void transport_electron(ctx_t *c, part_t *p) {
             return;
         }
         if (!hard) continue;
-        /* Woodcock acceptance at the end point with the end energy */
-        int m1 = c->geo->mat[v1];
-        double rho1 = c->geo->rho[v1];
+        /* Woodcock acceptance at the end point with the end energy (in the
+         * step's voxel with the per-voxel majorant) */
+        int m1 = (c->flags & OM_FLAG_VOXEL_EMAJOR) ? m0 : c->geo->mat[v1];
+        double rho1 = (c->flags & OM_FLAG_VOXEL_EMAJOR) ? rho0 : c->geo->rho[v1];
         double sm = rho1 * om_sigma_moller(&c->mats[m1], T1, P->t_c);
         double sb = rho1 * om_sigma_brem(&c->mats[m1], T1, P->k_c);
         if (sm + sb > sig_hat) {

@@ -83,8 +83,9 @@ struct __align__(16) Rec {
 
 // An electron whose step ended on a hard-event candidate (§II.B.3, the
 // electron Woodcock test), parked until its warp runs a converged hard pass:
-// the particle after its step, the majorant Sigma_hat of the step's start
-// energy and the voxel of the end point.  64 bytes.
+// the particle after its step, the majorant Sigma_hat of the step and the
+// step's voxel (where the candidate lies, and whose cross-section the
+// majorant bounds).  64 bytes.
 struct __align__(16) HardRec {
     Rec r;
     float sig_hat;

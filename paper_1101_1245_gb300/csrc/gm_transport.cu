@@ -24,6 +24,8 @@
 
 namespace gm {
 
+// Relative margin of the per-voxel electron hard-event majorant (2^-14).
+constexpr float kHardMajorantMargin = 1.00006103515625f;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int MAX_WARPS = 32;
 
@@ -573,7 +575,11 @@ __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, in
     // distance to the voxel faces along u, plus the nudge
     float dv = exit_distance(P, p, ix, iy, iz);
     dv = fmaxf(dv, 0.0f) + ph.nudge;
-    const float sig_hat = interp_ldg(P.maj + G, xe);
+    // The step stays in its voxel (it ends at the exit face, plus the nudge),
+    // so the voxel's own hard cross-section at the start energy bounds it over
+    // the step: Sigma_hard,m rises with T, and T only falls along the step.
+    // The margin covers the rounding of the two interpolations.
+    const float sig_hat = rho0 * interp(te + G, xe) * kHardMajorantMargin;
     const uint4 r = draw4(p, P);
     const float ehard = -__logf(u01(r.x)) / sig_hat;
     float es = fminf(dv, smax);
@@ -626,7 +632,7 @@ __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, in
         HardRec &h = A.hard[(size_t)gw * HARD_CAP + slot];
         h.r = make_rec(p);
         h.sig_hat = sig_hat;
-        h.idx = idx1;
+        h.idx = idx0;
         p.act = false;
     }
     return true;
@@ -636,14 +642,16 @@ __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, in
 // Electron hard event (GPUMCD §II.B.3): the electron Woodcock test at the end
 // of a step whose sampled hard distance was the shortest, then Moller or
 // bremsstrahlung.  Runs in the warp's hard pass with the parked candidate in
-// the lane: p after its step, sig_hat = Sigma_hat(E0), idx1 = its voxel.
+// the lane: p after its step, sig_hat = the step's majorant, idx1 = the step's
+// voxel, which holds the candidate point (the step ends inside it, or at most
+// the nudge past its face) and so the event and its sub-cut-off deposits.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void hard_event(const TransportArgs &A, const Smem &S, Lane &p, float sig_hat,
                                         uint32_t idx1, int gw, int w) {
     const PlanDev &P = S.plans[p.plan];
     const Phys &ph = A.phys;
     const uint32_t e1 = p.E;
-    // electron Woodcock: accept a real hard event with Sigma(end)/Sigma_hat(start)
+    // electron Woodcock: accept a real hard event with Sigma(T_end)/Sigma_hat
     const uint32_t vw1 = __ldg(P.vox + idx1);
     const int m1 = vw1 & (NMAT - 1);
     const float rho1 = (float)(vw1 >> 4) * kRhoQ;

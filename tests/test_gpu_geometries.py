@@ -22,6 +22,7 @@ density drives up, is a measured output of `bench.py --workload geoms`.
 import numpy as np
 import pytest
 
+import oracle
 import paper_1101_1245_gb300 as g
 import workloads as W
 from tests._stats import three_sigma_pass_rate
@@ -71,9 +72,14 @@ def test_paper_geometry_parity(ctx, geom, particle, n):
     rate = three_sigma_pass_rate(gpu.dose, gpu.sigma, do, so, mask)
     assert rate >= 0.99, rate
     st, os_ = gpu.stats, ora.stats
-    assert st["n_electron_steps"] / n == pytest.approx(os_["n_e_steps"] / n, rel=0.03)
     assert st["n_hard_real"] / n == pytest.approx(os_["n_hard_real"] / n, rel=0.05)
     assert st["n_photon_real"] / n == pytest.approx(os_["n_photon_real"] / n, rel=0.05)
+    # The GPU's electron Woodcock majorant is the step's own voxel's (the
+    # oracle's FLAG_VOXEL_EMAJOR form, which gives the paper form's dose): a
+    # lung or bone region splits fewer steps at fictitious candidates, so its
+    # step count is compared with the oracle run in that form.
+    ov = run_oracle(plan, mats=W.MATERIALS_PAPER, flags=oracle.FLAG_VOXEL_EMAJOR).stats
+    assert st["n_electron_steps"] / n == pytest.approx(ov["n_e_steps"] / n, rel=0.03)
 
 
 @pytest.mark.parametrize("energy", [1.0, 15.0])

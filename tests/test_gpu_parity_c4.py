@@ -26,7 +26,11 @@ of the voxels pass on two photon plans), so:
   freedom): >= 97% of a plan's blocks and >= 98.5% of all within 4 of it
   (an oracle against a second oracle run passes 99.2-100%);
 - the exact integer energy ledger of every plan, and event rates per history,
-  pooled by particle type, within 3%.
+  pooled by particle type, within 3%.  The GPU takes each electron step's
+  majorant from its own voxel (an exact Woodcock form that gives the paper
+  form's dose; tests/test_oracle_kinematics.py), which splits fewer steps at
+  fictitious candidates: its step rate is compared with an oracle run in that
+  form (a tenth of the histories), the other rates with the paper's form.
 The served form runs the same plans to the same tallies
 (tests/test_gpu_batched_served.py), so this also covers it.
 """
@@ -59,7 +63,8 @@ def _blocks(a, n):
 def _oracle_plan(args):
     """Worker: one plan of the batched workload on the oracle in K parts: its
     per-voxel dose and sigma in Gy per history, the energy per history of each
-    part in each block, and its event counts."""
+    part in each block, its event counts, and the electron steps per history
+    of a run in the GPU's per-voxel majorant form."""
     spec, n, seed = args
     ph = spec.phantom()
     src = W.square_field(spec.particle, spec.energy, ph, spec.field_cm)
@@ -74,6 +79,10 @@ def _oracle_plan(args):
         st = {k: st.get(k, 0) + v for k, v in pst.items()}
         parts.append(_blocks(p1, spec.n) / float(b - a))
     r = oracle.OracleResult(n, s1, s2, st)
+    nv = max(n // 10, 1000)
+    _, _, vst = oracle.simulate_range(W.MATERIALS, W.DEFAULT_PHYSICS, ph, src, n, n + nv, seed,
+                                      oracle.FLAG_VOXEL_EMAJOR)
+    st["n_e_steps_voxel_form"] = vst["n_e_steps"] * (n / nv)
     return spec.index, r.dose_gy(ph), r.sigma_gy(ph), np.array(parts), st
 
 
@@ -135,7 +144,7 @@ def test_batched_workload_plans_against_oracle():
             brates[idx] = (float(np.mean(np.abs(zb) <= 4.0)), int(pick.sum()))
             # a sequence's event counters go to its first plan: pool them by type
             t = specs[idx].particle
-            for k_g, k_o in (("n_photon_real", "n_photon_real"), ("n_electron_steps", "n_e_steps"),
+            for k_g, k_o in (("n_photon_real", "n_photon_real"), ("n_electron_steps", "n_e_steps_voxel_form"),
                              ("n_hard_real", "n_hard_real"), ("n_compton", "n_compton"),
                              ("n_pair", "n_pair"), ("n_brem", "n_brem"), ("n_moller", "n_moller")):
                 c = counts[t].setdefault(k_g, [0, 0.0])

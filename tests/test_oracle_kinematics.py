@@ -2,7 +2,8 @@
 not reach: the magnitudes of the pair and bremsstrahlung forms (against the
 textbook radiation length), the direction rotation and the Compton and Moller
 kinematics (against geometry and momentum conservation), the electron
-Woodcock acceptance (invariance to a raised majorant, GPUMCD §II.B.3) and the
+Woodcock acceptance (invariance to a raised majorant, and the per-voxel majorant
+form against the paper's, GPUMCD §II.B.3) and the
 history-by-history uncertainty estimator (§II.D) against the spread of
 independent runs.
 """
@@ -169,6 +170,45 @@ def test_electron_woodcock_invariance_far_dense_voxel():
     mask[23 * 16 * 16 + 15 * 16 + 15] = False
     assert mask.sum() > 50
     assert three_sigma_pass_rate(da, sa, db, sb, mask) >= 0.98
+
+
+def test_per_voxel_electron_majorant_gives_the_paper_forms_dose():
+    """Two exact electron Woodcock schemes (GPUMCD §II.B.3): the paper's
+    majorant over the whole phantom, tested at the step's end point, and each
+    step's own voxel cross-section at the start energy, tested in that voxel
+    (OM_FLAG_VOXEL_EMAJOR; a step stays in its voxel and Sigma_hard rises with
+    T).  On a smoothed-noise lung / water / bone phantom of the batched
+    workload the per-voxel form has almost no fictitious candidates, so fewer
+    steps.  The real hard-event rate and the dose agree within 4 sigma of the
+    parts' spread, over voxels chosen by the mean of both forms (a selection on
+    either one alone would favour its upward fluctuations)."""
+    sp = W.config4()[24]  # 64^3 at 0.46 cm, 13.6 MeV electrons
+    ph = sp.phantom()
+    src = W.square_field(sp.particle, sp.energy, ph, sp.field_cm)
+    n, parts = 96_000, 8
+    procs = min(host_cores(), 16)
+    a = oracle.simulate_parts(W.MATERIALS, P, ph, src, n, 21, parts, processes=procs)
+    b = oracle.simulate_parts(W.MATERIALS, P, ph, src, n, 22, parts, processes=procs,
+                              flags=oracle.FLAG_VOXEL_EMAJOR)
+    fict_a = sum(r.stats["n_hard_fict"] for r in a)
+    fict_b = sum(r.stats["n_hard_fict"] for r in b)
+    assert fict_b < 0.05 * fict_a, (fict_a, fict_b)
+    steps_a = sum(r.stats["n_e_steps"] for r in a)
+    steps_b = sum(r.stats["n_e_steps"] for r in b)
+    assert steps_b < 0.95 * steps_a, (steps_a, steps_b)
+    ra = np.array([r.stats["n_hard_real"] for r in a], dtype=float)
+    rb = np.array([r.stats["n_hard_real"] for r in b], dtype=float)
+    se = math.sqrt(ra.var(ddof=1) / parts + rb.var(ddof=1) / parts)
+    assert abs(ra.mean() - rb.mean()) <= 4.0 * se, (ra.mean(), rb.mean(), se)
+    da = np.array([r.dose_gy(ph) for r in a])
+    db = np.array([r.dose_gy(ph) for r in b])
+    sel = 0.5 * (da.mean(0) + db.mean(0))
+    for frac in (0.5, 0.1):
+        m = sel > frac * sel.max()
+        ma, mb = da[:, m].mean(1), db[:, m].mean(1)
+        se = math.sqrt(ma.var(ddof=1) / parts + mb.var(ddof=1) / parts)
+        assert abs(ma.mean() - mb.mean()) <= 4.0 * se, (frac, ma.mean(), mb.mean(), se)
+        assert se < 0.003 * ma.mean()  # the comparison resolves 1% differences
 
 
 def test_history_by_history_sigma_matches_the_spread_of_independent_runs():
