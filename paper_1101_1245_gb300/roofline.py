@@ -60,10 +60,10 @@ INST_PER_EVENT_C4_E_SEQ: Optional[float] = 17.43
 INST_PER_EVENT_C4_PH_SEQ: Optional[float] = 17.65
 # DRAM bytes (read + write) per event of the same case on the current kernel (one
 # 1024-thread CTA per SM, tables packed per material, a photon's majorant taken once
-# per pass): 1.935 GB over 259.66e6 events (electron sequence) and 1.885 GB over
-# 128.58e6 (photon sequence)
-TRAFFIC_BYTES_PER_EVENT_C4_E_SEQ: Optional[float] = 7.45
-TRAFFIC_BYTES_PER_EVENT_C4_PH_SEQ: Optional[float] = 14.66
+# per pass, each electron step's majorant from its own voxel): 1.920 GB over
+# 247.16e6 events (electron sequence) and 1.820 GB over 124.71e6 (photon sequence)
+TRAFFIC_BYTES_PER_EVENT_C4_E_SEQ: Optional[float] = 7.77
+TRAFFIC_BYTES_PER_EVENT_C4_PH_SEQ: Optional[float] = 14.59
 
 
 def alu_roofline_c4(events_e_seq: int, events_ph_seq: int, kernel_ms: float, sm_mhz: Optional[float],
