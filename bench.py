@@ -694,19 +694,31 @@ def run_c4(args):
     out_d = [torch.empty(ph.nvox, dtype=torch.float64, pin_memory=True).numpy() for ph in phantoms]
     out_s = [torch.empty(ph.nvox, dtype=torch.float64, pin_memory=True).numpy() for ph in phantoms]
 
+    phases = {}
+
     def e2e_step(step):
+        t = [time.perf_counter()]
         pid2 = [ctx.create_phantom(ph) for ph in ph_host]
+        t.append(time.perf_counter())
         pl2 = [ctx.plan_open(pid, src, sd, W_C4) for pid, src, sd in zip(pid2, srcs, seeds(step))]
+        t.append(time.perf_counter())
         r = ctx.run_to_uncertainty(pl2, first, caps, TARGET, THRESHOLD)
+        t.append(time.perf_counter())
         for p, d, s_ in zip(pl2, out_d, out_s):
             ctx.plan_result_host(p, THRESHOLD, d, s_)
+        t.append(time.perf_counter())
         for p in pl2:
             ctx.plan_close(p)
         for pid in pid2:
             ctx.destroy_phantom(pid)
+        t.append(time.perf_counter())
+        for k, a, b in zip(("create_phantoms", "plan_open", "run_to_uncertainty", "plan_result_host", "close"),
+                           t[:-1], t[1:]):
+            phases.setdefault(k, []).append(1e3 * (b - a))
         return sum(r["histories"])
 
     e2e_step(0)  # warm-up (fills the device-memory cache)
+    phases.clear()
     e2e = []
     for i in range(2):
         torch.cuda.synchronize()
@@ -765,7 +777,8 @@ def run_c4(args):
             "roofline": roof,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "host_memory": "pinned", "steps": len(e2e),
-                    "form": "64 phantoms uploaded, run to 1% batched, dose and sigma read back, per step"},
+                    "form": "64 phantoms uploaded, run to 1% batched, dose and sigma read back, per step",
+                    "phases_ms": {k: statistics.median(v) for k, v in phases.items()}},
             "gpu_launches": launches,
             "clocks": clocks}
     if cpu:
