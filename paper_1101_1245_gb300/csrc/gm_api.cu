@@ -95,6 +95,7 @@ struct gpumcd_ctx {
     int n_sm = 0;
     cudaStream_t stream = nullptr;
     uint64_t budget = 0, used = 0;
+    uint64_t cache_max = 32ull << 30;  // without a budget: half the device's memory, at least 32 GB
     bool tables = false;
     int n_mat = 0;
     gpumcd_physics phys{};
@@ -143,8 +144,9 @@ gpumcd_status cuda_status(cudaError_t e) {
 // sequence in flight).  A block enters the cache only when no GPU work on it
 // is pending: every caller of dev_free has synchronized the streams that used
 // it.  The budget counts live bytes; live + cached bytes stay within it, and
-// without a budget the cache keeps at most kCacheMax bytes.
-constexpr uint64_t kCacheMax = 32ull << 30;
+// without a budget the cache keeps at most cache_max bytes: half of the
+// device's memory (at least 32 GB), so a working set of tens of GB (the
+// tallies of 64 plans) cycles through the cache and never through cudaFree.
 
 void cache_trim(gpumcd_ctx *c, uint64_t limit) {
     while (c->cached > limit && !c->cache.empty()) {
@@ -161,7 +163,7 @@ void dev_free(gpumcd_ctx *c, DevBuf &b) {
         c->cache.emplace(b.bytes, b.p);
         c->cached += b.bytes;
         if (c->budget) cache_trim(c, c->budget > c->used ? c->budget - c->used : 0);
-        else cache_trim(c, kCacheMax);
+        else cache_trim(c, c->cache_max);
     }
     b.p = nullptr;
     b.bytes = 0;
@@ -326,6 +328,9 @@ gpumcd_status gpumcd_init(gpumcd_ctx **out, int32_t device, uint64_t hbm_budget_
     c->budget = hbm_budget_bytes;
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
+    size_t mem_free = 0, mem_total = 0;
+    if (e == cudaSuccess) e = cudaMemGetInfo(&mem_free, &mem_total);
+    if (e == cudaSuccess) c->cache_max = std::max<uint64_t>(c->cache_max, mem_total / 2);
     // The context stream (tables, phantoms, folds, gpumcd_run by default) has
     // the highest priority, so a fold takes SMs first as a submitted
     // transport sequence drains; submitted sequences run at the lowest.
