@@ -50,7 +50,12 @@ SOURCES = {
     "grouped_phsp": W.Source(W.ELECTRON, W.BEAM_PHASE_SPACE,
                              phase_space=W.polyenergetic_phase_space(W.ELECTRON, _plan(), 1013, seed=7).phase_space,
                              energy_grouping=W.ENERGY_GROUPED),
+    # the same phase space ungrouped (the phase-space kernel, claims in history order)
+    "phsp": W.Source(W.ELECTRON, W.BEAM_PHASE_SPACE,
+                     phase_space=W.polyenergetic_phase_space(W.ELECTRON, _plan(), 1013, seed=7).phase_space),
 }
+# sources that run the phase-space kernel
+PHSP_KINDS = ("grouped", "grouped_phsp", "phsp")
 
 
 def _phsp_kernel_accepts(launch) -> bool:
@@ -69,7 +74,7 @@ def reference():
     return ph, out
 
 
-@pytest.mark.parametrize("kind", ["electron", "photon", "grouped", "grouped_phsp"])
+@pytest.mark.parametrize("kind", ["electron", "photon", "grouped", "grouped_phsp", "phsp"])
 @pytest.mark.parametrize("launch", [
     dict(),
     dict(block_threads=512, blocks_per_sm=2),
@@ -87,7 +92,7 @@ def reference():
     dict(refill_period=g.REFILL_WHEN_EMPTY),
 ])
 def test_bit_identical_across_launch_shapes(reference, kind, launch):
-    if kind.startswith("grouped") and not _phsp_kernel_accepts(launch):
+    if kind in PHSP_KINDS and not _phsp_kernel_accepts(launch):
         pytest.skip("outside the phase-space kernel's launch restrictions")
     ph, out = reference
     ctx = make_ctx(**launch)
