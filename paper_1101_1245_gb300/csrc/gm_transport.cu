@@ -19,6 +19,12 @@
 // Randomness is a counter-based Philox keyed by the plan seed with counter
 // (draw, lineage lo, lineage hi, history), and energies are integers, so the
 // tally is independent of how particles are scheduled.
+//
+// Divisions on the event path are written __fdividef (reciprocal, then
+// multiply): every divisor there is a direction cosine, an energy, a cross
+// section or a sampler constant, far below the 2^126 where that form departs
+// from the approximate division this file is compiled with (-prec-div=false),
+// so the quotients are the same and the range handling is skipped.
 #include "gm_common.cuh"
 #include "gm_host.h"
 
@@ -110,9 +116,9 @@ __device__ __forceinline__ uint32_t voxel_index(const PlanDev &P, float x, float
 // Distance along the direction to the exit face of voxel (ix, iy, iz).
 __device__ __forceinline__ float exit_distance(const PlanDev &P, const Lane &p, int ix, int iy, int iz) {
     float dv = 3.0e38f;
-    if (p.ux != 0.f) dv = fminf(dv, ((p.ux > 0.f ? (float)(ix + 1) : (float)ix) - p.x * P.inv_dx) * P.dx / p.ux);
-    if (p.uy != 0.f) dv = fminf(dv, ((p.uy > 0.f ? (float)(iy + 1) : (float)iy) - p.y * P.inv_dy) * P.dy / p.uy);
-    if (p.uz != 0.f) dv = fminf(dv, ((p.uz > 0.f ? (float)(iz + 1) : (float)iz) - p.z * P.inv_dz) * P.dz / p.uz);
+    if (p.ux != 0.f) dv = fminf(dv, __fdividef(((p.ux > 0.f ? (float)(ix + 1) : (float)ix) - p.x * P.inv_dx) * P.dx, p.ux));
+    if (p.uy != 0.f) dv = fminf(dv, __fdividef(((p.uy > 0.f ? (float)(iy + 1) : (float)iy) - p.y * P.inv_dy) * P.dy, p.uy));
+    if (p.uz != 0.f) dv = fminf(dv, __fdividef(((p.uz > 0.f ? (float)(iz + 1) : (float)iz) - p.z * P.inv_dz) * P.dz, p.uz));
     return dv;
 }
 
@@ -243,7 +249,7 @@ __device__ __forceinline__ Rec make_rec(const Lane &p) {
 constexpr int SAMPLER_CAP = 4096;  // proposals before a sampler gives up (counted, never expected)
 
 __device__ float sample_kn(Lane &p, const PlanDev &P, float k, float *c, uint32_t *w4, unsigned *capped) {
-    const float e0 = 1.0f / (1.0f + 2.0f * k);
+    const float e0 = __fdividef(1.0f, 1.0f + 2.0f * k);
     const float a1 = __logf(1.0f + 2.0f * k);
     const float a2 = 0.5f * (1.0f - e0 * e0);
     for (int it = 0;; ++it) {
@@ -253,9 +259,9 @@ __device__ float sample_kn(Lane &p, const PlanDev &P, float k, float *c, uint32_
             eps = __expf(-a1 * u01(r.y));
         else
             eps = sqrtf(fmaf(1.0f - e0 * e0, u01(r.y), e0 * e0));
-        const float t = (1.0f - eps) / (k * eps);
+        const float t = __fdividef(1.0f - eps, k * eps);
         const float s2 = t * (2.0f - t);
-        const bool ok = u01(r.z) <= 1.0f - eps * s2 / (1.0f + eps * eps);
+        const bool ok = u01(r.z) <= 1.0f - __fdividef(eps * s2, 1.0f + eps * eps);
         if (ok || it >= SAMPLER_CAP) {
             if (!ok) ++*capped;
             *c = 1.0f - t;
@@ -269,16 +275,16 @@ __device__ float sample_kn(Lane &p, const PlanDev &P, float k, float *c, uint32_
 // nu/(A+nu)^3 and accepted with (2-nu)(1/(A+nu)+B) / (2(1/A+B)).
 __device__ float sample_sauter(Lane &p, const PlanDev &P, float T, uint32_t *w3, unsigned *capped) {
     const float g = 1.0f + T / kMC2f;
-    const float b2 = 1.0f - 1.0f / (g * g);
+    const float b2 = 1.0f - __fdividef(1.0f, g * g);
     const float beta = sqrtf(b2);
-    const float A = (1.0f / (g * g * (1.0f + beta))) / beta;
+    const float A = __fdividef(__fdividef(1.0f, g * g * (1.0f + beta)), beta);
     const float B = 0.5f * beta * g * (g - 1.0f) * (g - 2.0f);
-    const float gmax = 2.0f * (1.0f / A + B);
+    const float gmax = 2.0f * (__fdividef(1.0f, A) + B);
     for (int it = 0;; ++it) {
         const uint4 r = draw4(p, P);
         const float sq = sqrtf(u01(r.x));
-        const float nu = 2.0f * A * sq / (A + 2.0f - 2.0f * sq);
-        const bool ok = u01(r.y) * gmax <= (2.0f - nu) * (1.0f / (A + nu) + B);
+        const float nu = __fdividef(2.0f * A * sq, A + 2.0f - 2.0f * sq);
+        const bool ok = u01(r.y) * gmax <= (2.0f - nu) * (__fdividef(1.0f, A + nu) + B);
         if (ok || it >= SAMPLER_CAP) {
             if (!ok) ++*capped;
             *w3 = r.z;
@@ -290,14 +296,14 @@ __device__ float sample_sauter(Lane &p, const PlanDev &P, float T, uint32_t *w3,
 // Moller knock-on fraction in [t_c/T, 1/2] (§II.B.1): 1/eps^2 proposal.
 __device__ float sample_moller(Lane &p, const PlanDev &P, float T, float t_c, uint32_t *w3, unsigned *capped) {
     const float g = T / kMC2f + 1.0f;
-    const float c1 = (g - 1.0f) * (g - 1.0f) / (g * g);
-    const float c2 = (2.0f * g - 1.0f) / (g * g);
-    const float ec = t_c / T;
+    const float c1 = __fdividef((g - 1.0f) * (g - 1.0f), g * g);
+    const float c2 = __fdividef(2.0f * g - 1.0f, g * g);
+    const float ec = __fdividef(t_c, T);
     const float bound = 2.0f + 0.25f * c1;
     for (int it = 0;; ++it) {
         const uint4 r = draw4(p, P);
-        const float eps = ec / (1.0f - u01(r.x) * (1.0f - 2.0f * ec));
-        const float q = eps / (1.0f - eps);
+        const float eps = __fdividef(ec, 1.0f - u01(r.x) * (1.0f - 2.0f * ec));
+        const float q = __fdividef(eps, 1.0f - eps);
         const float f = 1.0f + q * q + c1 * eps * eps - c2 * q;
         const bool ok = u01(r.y) * bound <= f;
         if (ok || it >= SAMPLER_CAP) {
@@ -313,11 +319,11 @@ __device__ float sample_moller(Lane &p, const PlanDev &P, float T, float t_c, ui
 __device__ float sample_brem(Lane &p, const PlanDev &P, float T, float k_c, float cA, float c1,
                              uint32_t *w3, unsigned *capped) {
     const float E = T + kMC2f;
-    const float lr = __logf(T / k_c);
+    const float lr = __logf(__fdividef(T, k_c));
     for (int it = 0;; ++it) {
         const uint4 r = draw4(p, P);
         const float k = k_c * __expf(u01(r.x) * lr);
-        const float y = k / E;
+        const float y = __fdividef(k, E);
         const float gy = fmaf(y, y - 4.0f / 3.0f, 4.0f / 3.0f) * cA + (1.0f - y) * c1;
         const bool ok = u01(r.y) <= gy;
         if (ok || it >= SAMPLER_CAP) {
@@ -336,7 +342,7 @@ __device__ __forceinline__ float ms_mu(const float *tab, const Grid &gr, float g
     const float a = __expf(interp_ms(tab + TAB_MS, fmaf(__log2f(g1), gr.ms_a, gr.ms_b)));
     // at z = 1 the exact value is 1; in FP32, 1 + a rounds to 1 when a < 2^-24
     // and the quotient would be a / 0
-    return fminf(a * z / (1.0f + a - z), 1.0f);
+    return fminf(__fdividef(a * z, 1.0f + a - z), 1.0f);
 }
 
 __device__ __forceinline__ float sample_spectrum(const PlanDev &P, float z) {
@@ -423,7 +429,7 @@ __device__ __forceinline__ bool photon_flight(const TransportArgs &A, const Smem
         return false;
     }
     const uint4 r = draw4(p, P);
-    const float s = -__logf(u01(r.x)) / mu_hat;
+    const float s = __fdividef(-__logf(u01(r.x)), mu_hat);
     p.x = fmaf(s, p.ux, p.x);
     p.y = fmaf(s, p.uy, p.y);
     p.z = fmaf(s, p.uz, p.z);
@@ -528,7 +534,7 @@ __device__ __forceinline__ void photon_interact(const TransportArgs &A, const Sm
         for (int j = 0; j < 2; ++j) {
             const uint32_t te = j == 0 ? t1 : t2;
             if (te >= ph.e_abs_q) {
-                const float th = kMC2f / ((float)te * kQf + kMC2f);
+                const float th = __fdividef(kMC2f, (float)te * kQf + kMC2f);
                 float st, ct;
                 __sincosf(th, &st, &ct);
                 float vx = p.ux, vy = p.uy, vz = p.uz;
@@ -560,6 +566,8 @@ __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, in
     int ix, iy, iz;
     const uint32_t idx0 = voxel_index(P, p.x, p.y, p.z, ix, iy, iz);
     const uint32_t vw = __ldg(P.vox + idx0);
+    // the step's draw, taken while the voxel word is on its way
+    const uint4 r = draw4(p, P);
     const int m0 = vw & (NMAT - 1);
     const float rho0 = (float)(vw >> 4) * kRhoQ;
     if (p.E < ph.e_abs_q) {
@@ -571,7 +579,7 @@ __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, in
     const float T = (float)p.E * kQf;
     const float xe = fmaf(__log2f((float)p.E), ph.grid.el_a, ph.grid.el_bq);
     const float L0 = rho0 * interp(te, xe);
-    const float smax = ph.estepe * T / L0;
+    const float smax = __fdividef(ph.estepe * T, L0);
     // distance to the voxel faces along u, plus the nudge
     float dv = exit_distance(P, p, ix, iy, iz);
     dv = fmaxf(dv, 0.0f) + ph.nudge;
@@ -580,8 +588,7 @@ __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, in
     // the step: Sigma_hard,m rises with T, and T only falls along the step.
     // The margin covers the rounding of the two interpolations.
     const float sig_hat = rho0 * interp(te + G, xe) * kHardMajorantMargin;
-    const uint4 r = draw4(p, P);
-    const float ehard = -__logf(u01(r.x)) / sig_hat;
+    const float ehard = __fdividef(-__logf(u01(r.x)), sig_hat);
     float es = fminf(dv, smax);
     const bool hard = ehard < es;
     es = fminf(es, ehard);
@@ -653,6 +660,7 @@ __device__ __forceinline__ void hard_event(const TransportArgs &A, const Smem &S
     const uint32_t e1 = p.E;
     // electron Woodcock: accept a real hard event with Sigma(T_end)/Sigma_hat
     const uint32_t vw1 = __ldg(P.vox + idx1);
+    const uint4 r2 = draw4(p, P);  // the event's draw, taken while the voxel word loads
     const int m1 = vw1 & (NMAT - 1);
     const float rho1 = (float)(vw1 >> 4) * kRhoQ;
     const float *t1 = S.tab + tab_el(m1);
@@ -663,7 +671,6 @@ __device__ __forceinline__ void hard_event(const TransportArgs &A, const Smem &S
     const float sb = T1 > ph.k_c ? rho1 * interp(t1 + 2 * G, xe1) : 0.0f;
     const float sm = T1 > 2.0f * ph.t_c ? fmaxf(rho1 * interp(t1 + G, xe1) - sb, 0.0f) : 0.0f;
     const float sig = sm + sb;
-    const uint4 r2 = draw4(p, P);
     if (u01(r2.x) * sig_hat >= sig) {
         count(S, CNT_HARD_FICT);
         return;
@@ -679,8 +686,8 @@ __device__ __forceinline__ void hard_event(const TransportArgs &A, const Smem &S
         const uint32_t tk = min(e1, __float2uint_rn(eps * (float)e1));
         const uint32_t tp = e1 - tk;
         const float tkf = (float)tk * kQf, tpf = (float)tp * kQf;
-        const float ck = sqrtf(fminf(1.0f, tkf * (T1 + 2.0f * kMC2f) / (T1 * (tkf + 2.0f * kMC2f))));
-        const float cpp = sqrtf(fminf(1.0f, tpf * (T1 + 2.0f * kMC2f) / (T1 * (tpf + 2.0f * kMC2f))));
+        const float ck = sqrtf(fminf(1.0f, __fdividef(tkf * (T1 + 2.0f * kMC2f), T1 * (tkf + 2.0f * kMC2f))));
+        const float cpp = sqrtf(fminf(1.0f, __fdividef(tpf * (T1 + 2.0f * kMC2f), T1 * (tpf + 2.0f * kMC2f))));
         float sp, cp;
         __sincosf(kTWO_PIf * u01(w3), &sp, &cp);
         float vx = p.ux, vy = p.uy, vz = p.uz;
@@ -700,7 +707,7 @@ __device__ __forceinline__ void hard_event(const TransportArgs &A, const Smem &S
                                     &capped);
         if (capped) atomicAdd(&S.cnt[CNT_SAMPLER_CAP], 1ull);
         const uint32_t kq = min(e1, __float2uint_rn(k * kInvQf));
-        const float th = kMC2f / (T1 + kMC2f);
+        const float th = __fdividef(kMC2f, T1 + kMC2f);
         float st, ct, sp, cp;
         __sincosf(th, &st, &ct);
         __sincosf(kTWO_PIf * u01(w3), &sp, &cp);
