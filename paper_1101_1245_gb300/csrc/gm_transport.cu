@@ -558,11 +558,6 @@ __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, in
                               uint32_t &dep_idx, uint32_t &dep_e) {
     const PlanDev &P = S.plans[p.plan];
     const Phys &ph = A.phys;
-    if (!inside(P, p.x, p.y, p.z)) {  // a primary aimed outside the phantom
-        ledger_add(S, p.plan, 1, p.E);
-        p.act = false;
-        return false;
-    }
     int ix, iy, iz;
     const uint32_t idx0 = voxel_index(P, p.x, p.y, p.z, ix, iy, iz);
     const uint32_t vw = __ldg(P.vox + idx0);
@@ -854,6 +849,12 @@ __device__ int refill(const TransportArgs &A, const Smem &S, CtaFlags &F, Lane &
             // decreasing order of their energy (the order its launch sorted)
             if (PHSP && P.e_group && j < P.n_sorted) j = __ldg(P.order + j);
             ledger_add(S, plan, 0, make_primary<PHSP>(p, P, plan, P.hist_base + j));
+            if (!KERMA && t == 1 && !inside(P, p.x, p.y, p.z)) {
+                // an electron primary aimed outside the phantom escapes at once
+                // (every other electron starts its steps inside)
+                ledger_add(S, plan, 1, p.E);
+                p.act = false;
+            }
             if (KERMA && t == 1) {
                 // photon-only mode: a primary electron deposits where it enters
                 if (inside(P, p.x, p.y, p.z)) {
