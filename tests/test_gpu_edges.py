@@ -1,6 +1,8 @@
 """Edge and degenerate cases of the CUDA path: empty and ragged inputs, beams
 that miss the phantom, sources below the cut-offs, one-voxel phantoms, and
 invalid inputs rejected with a status instead of a fault."""
+import math
+
 import numpy as np
 import pytest
 
@@ -41,6 +43,27 @@ def test_beam_missing_the_phantom_escapes_whole(ctx, particle):
     assert st["e_incident"] == 3000 * round(5.0 / Q)
     assert st["e_escaped"] == st["e_incident"] and st["e_deposited"] == 0
     assert not r.dose.any()
+
+
+def test_electron_field_wider_than_the_phantom(ctx):
+    """An electron field wider than the phantom's entry face: the primaries that
+    start outside escape as they are claimed, the others are transported.  The
+    escaped fraction and the dose agree with the oracle; the ledger is exact."""
+    ph = W.homogeneous((10, 10, 12), 0.5, W.MAT_WATER, 1.0)  # a 5 x 5 cm face
+    src = W.Source(W.ELECTRON, W.BEAM_SQUARE, energy=6.0, center_cm=(2.5, 2.5), field_cm=8.0)
+    plan = W.Plan("wide", ph, src, 40_000, 8)
+    gres = run_gpu(ctx, plan)
+    ores = run_oracle(plan)
+    assert ledger_exact(gres.stats)
+    fg = gres.stats["e_escaped"] / gres.stats["e_incident"]
+    fo = ores.stats["e_escaped"] / ores.stats["e_incident"]
+    # 1 - (5/8)^2 = 61% of the field lies outside the face
+    assert fg > 1.0 - (5.0 / 8.0) ** 2 - 0.01
+    # a history's escaped fraction lies in [0, 1]: its variance is at most p (1 - p)
+    assert abs(fg - fo) <= 4.0 * math.sqrt(2.0 * fg * (1.0 - fg) / plan.n_histories), (fg, fo)
+    do, so = ores.dose_gy(ph), ores.sigma_gy(ph)
+    mask = do > 0.1 * do.max()
+    assert three_sigma_pass_rate(gres.dose, gres.sigma, do, so, mask) >= 0.99
 
 
 def test_sources_below_the_cutoffs_deposit_at_entry(ctx):
