@@ -418,16 +418,6 @@ __device__ __forceinline__ bool photon_flight(const TransportArgs &A, const Smem
                                               float &rho_out, float &mu_out) {
     const PlanDev &P = S.plans[p.plan];
     const Phys &ph = A.phys;
-    if (p.E < ph.p_cut_q) {
-        if (inside(P, p.x, p.y, p.z)) {
-            int ix, iy, iz;
-            deposit(P, p.hist, voxel_index(P, p.x, p.y, p.z, ix, iy, iz), p.E);
-        } else {
-            ledger_add(S, p.plan, 1, p.E);
-        }
-        p.act = false;
-        return false;
-    }
     const uint4 r = draw4(p, P);
     const float s = __fdividef(-__logf(u01(r.x)), mu_hat);
     p.x = fmaf(s, p.ux, p.x);
@@ -849,6 +839,18 @@ __device__ int refill(const TransportArgs &A, const Smem &S, CtaFlags &F, Lane &
             // decreasing order of their energy (the order its launch sorted)
             if (PHSP && P.e_group && j < P.n_sorted) j = __ldg(P.order + j);
             ledger_add(S, plan, 0, make_primary<PHSP>(p, P, plan, P.hist_base + j));
+            if (t == 0 && p.E < A.phys.p_cut_q) {
+                // a photon primary below the photon cut-off deposits where it
+                // starts, or escapes from outside (every other photon flies
+                // above the cut-off)
+                if (inside(P, p.x, p.y, p.z)) {
+                    int ix, iy, iz;
+                    deposit(P, p.hist, voxel_index(P, p.x, p.y, p.z, ix, iy, iz), p.E);
+                } else {
+                    ledger_add(S, plan, 1, p.E);
+                }
+                p.act = false;
+            }
             if (!KERMA && t == 1 && !inside(P, p.x, p.y, p.z)) {
                 // an electron primary aimed outside the phantom escapes at once
                 // (every other electron starts its steps inside)
