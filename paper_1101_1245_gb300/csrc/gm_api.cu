@@ -86,6 +86,7 @@ struct Slot {
     cudaGraphExec_t gexec = nullptr;
     cudaGraphNode_t knode = nullptr;
     int g_grid = 0, g_block = 0, g_bps = 0;
+    const void *g_fn = nullptr;  // the transport kernel the graph holds
 };
 
 }  // namespace
@@ -709,7 +710,10 @@ void first_queues(gpumcd_ctx *c, Slot &sl) {
 gpumcd_status first_launch_graph(gpumcd_ctx *c, Slot &sl) {
     first_queues(c, sl);
     Control *dc = (Control *)sl.control.p;
-    if (!sl.gexec || sl.g_grid != sl.grid || sl.g_block != sl.block || sl.g_bps != sl.bps) {
+    // a graph is rebuilt for a new launch shape or another compiled kernel
+    // (its kernel node keeps the function it was captured with)
+    const void *fn = transport_kernel(sl.A, sl.block, sl.bps);
+    if (!sl.gexec || sl.g_grid != sl.grid || sl.g_block != sl.block || sl.g_bps != sl.bps || sl.g_fn != fn) {
         if (sl.gexec) cudaGraphExecDestroy(sl.gexec);
         if (sl.graph) cudaGraphDestroy(sl.graph);
         sl.gexec = nullptr;
@@ -744,6 +748,7 @@ gpumcd_status first_launch_graph(gpumcd_ctx *c, Slot &sl) {
         sl.g_grid = sl.grid;
         sl.g_block = sl.block;
         sl.g_bps = sl.bps;
+        sl.g_fn = fn;
     } else {
         cudaKernelNodeParams kp;
         CK(cudaGraphKernelNodeGetParams(sl.knode, &kp));

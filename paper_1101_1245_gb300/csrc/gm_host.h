@@ -44,6 +44,9 @@ cudaError_t launch_philox(const uint32_t *ctr, uint2 key, uint64_t n, int curand
 size_t transport_smem_bytes(uint32_t tab_bytes);
 cudaError_t transport_configure();
 cudaError_t launch_transport(const TransportArgs &a, int grid, int block, int blocks_per_sm, cudaStream_t s);
+// The transport kernel launch_transport runs for these arguments and shape
+// (null when no compiled kernel covers them).
+const void *transport_kernel(const TransportArgs &a, int block, int blocks_per_sm);
 // Claim order of a spectrum or phase space grouped by energy: order[0..n) =
 // offsets j of the histories hist_base + j of plan P, in decreasing order of
 // their primary's energy bin; count (GPUMCD_MAX_SPECTRUM_BINS unsigned) and

@@ -1199,10 +1199,14 @@ cudaError_t transport_configure() {
     return cudaSuccess;
 }
 
-cudaError_t launch_transport(const TransportArgs &a, int grid, int block, int blocks_per_sm, cudaStream_t s) {
-    TransportKernel fn = pick_variant(block, blocks_per_sm, (a.flags & GPUMCD_LAUNCH_PROFILE) != 0u,
+const void *transport_kernel(const TransportArgs &a, int block, int blocks_per_sm) {
+    return (const void *)pick_variant(block, blocks_per_sm, (a.flags & GPUMCD_LAUNCH_PROFILE) != 0u,
                                       (a.flags & GPUMCD_LAUNCH_WARP_AGGREGATE) != 0u, a.refill_period != 1u,
                                       (a.flags & GPUMCD_LAUNCH_KERMA) != 0u, a.phsp != 0u);
+}
+
+cudaError_t launch_transport(const TransportArgs &a, int grid, int block, int blocks_per_sm, cudaStream_t s) {
+    TransportKernel fn = (TransportKernel)transport_kernel(a, block, blocks_per_sm);
     if (!fn) return cudaErrorInvalidConfiguration;
     if (a.tab_bytes < tab_bytes(1) || a.tab_bytes > (uint32_t)TAB_BYTES) return cudaErrorInvalidValue;
     fn<<<grid, block, transport_smem_bytes(a.tab_bytes), s>>>(a);

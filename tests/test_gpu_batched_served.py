@@ -207,6 +207,35 @@ def test_graph_launches_equal_direct_launches():
         assert y[2]["e_deposited"] + y[2]["e_escaped"] + y[2]["e_rest"] == y[2]["e_incident"]
 
 
+def test_graph_follows_the_compiled_kernel():
+    """One slot's captured graph holds one compiled transport kernel.  When the
+    next run needs another one (a phase-space source runs its own kernel, the
+    photon-only flag another) at the same launch shape, the graph is captured
+    again, so each run gives the tally of a direct launch."""
+    ph = W.homogeneous((16, 16, 20), 0.5, W.MAT_WATER, 1.0)
+    beam = W.Source(W.ELECTRON, W.BEAM_SQUARE, energy=8.0, center_cm=(4.0, 4.0), field_cm=3.0)
+    phsp = W.Source(W.ELECTRON, W.BEAM_PHASE_SPACE,
+                    phase_space=W.polyenergetic_phase_space(W.ELECTRON, ph, 501, seed=9).phase_space)
+    gamma = W.Source(W.PHOTON, W.BEAM_SQUARE, energy=6.0, center_cm=(4.0, 4.0), field_cm=3.0)
+    steps = [(beam, 0), (phsp, 0), (beam, 0), (gamma, g.LAUNCH_KERMA), (gamma, 0)]
+    out = {}
+    for graph in (0, g.LAUNCH_GRAPH):
+        ctx = make_ctx()
+        pid = ctx.create_phantom(ph)
+        res = []
+        for i, (src, flags) in enumerate(steps):
+            ctx.set_launch(flags=flags | graph)
+            plan = ctx.plan_open(pid, src, 70 + i, 16)
+            ctx.run([plan], [20_000])
+            res.append(_dose(ctx, plan, ph.nvox))
+            ctx.plan_close(plan)
+        out[graph] = res
+        ctx.close()
+    for x, y in zip(out[0], out[g.LAUNCH_GRAPH]):
+        assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+        assert x[2]["e_deposited"] == y[2]["e_deposited"]
+
+
 def test_run_to_uncertainty_batched_equals_plans_alone():
     """gpumcd_run_to_uncertainty (§II.D: run until s_0.5 reaches the target):
     six uneven plans together and each plan by itself take the same rounds of
