@@ -60,10 +60,12 @@ INST_PER_EVENT_C4_E_SEQ: Optional[float] = 17.43
 INST_PER_EVENT_C4_PH_SEQ: Optional[float] = 17.65
 # DRAM bytes (read + write) per event of the same case on the current kernel (one
 # 1024-thread CTA per SM, tables packed per material, a photon's majorant taken once
-# per pass, each electron step's majorant from its own voxel): 1.920 GB over
-# 247.16e6 events (electron sequence) and 1.820 GB over 124.71e6 (photon sequence)
-TRAFFIC_BYTES_PER_EVENT_C4_E_SEQ: Optional[float] = 7.77
-TRAFFIC_BYTES_PER_EVENT_C4_PH_SEQ: Optional[float] = 14.59
+# per pass, each electron step's majorant from its own voxel, event-path divisions as
+# reciprocal-multiply, the step's draw taken while its voxel word loads, the inside
+# and cut-off tests of primaries at their claim): 1.907 GB over 247.16e6 events
+# (electron sequence) and 1.817 GB over 124.71e6 (photon sequence)
+TRAFFIC_BYTES_PER_EVENT_C4_E_SEQ: Optional[float] = 7.71
+TRAFFIC_BYTES_PER_EVENT_C4_PH_SEQ: Optional[float] = 14.57
 
 
 def alu_roofline_c4(events_e_seq: int, events_ph_seq: int, kernel_ms: float, sm_mhz: Optional[float],
