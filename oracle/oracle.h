@@ -17,8 +17,10 @@
  *  - cross-sections are closed forms evaluated exactly at each energy; the
  *    oracle uses no tables.
  *
- * Parity status: every function below is pinned by a -m "not gpu" test except
- * where the test file says "parity unpinned".
+ * Parity status: every function below is pinned by a -m "not gpu" test against
+ * mathematics or published values other than its own formula.  The identity of
+ * the Philox generator with the published Philox4x32-10 is pinned on the GPU,
+ * against cuRAND's generator.
  */
 #ifndef GPUMCD_ORACLE_H
 #define GPUMCD_ORACLE_H

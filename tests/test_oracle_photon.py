@@ -68,6 +68,38 @@ def test_photoelectric_scaling():
     assert 0.1 < expect < 0.4  # tabulated water photoelectric at 30 keV is ~0.15 cm^2/g
 
 
+def _sauter_k_shell(Z: int, k: float) -> float:
+    """Sauter's relativistic Born cross-section per atom for the K-shell photo
+    effect, binding neglected in the final state (Heitler, The Quantum Theory of
+    Radiation, section 21): (3/2) sigma_T Z^5 alpha^4 k^-5 (g^2 - 1)^(3/2)
+    [4/3 + g (g - 2) / (g + 1) (1 - ln(g + sqrt(g^2 - 1)) / (g sqrt(g^2 - 1)))],
+    with k = E / mc^2 and g = k + 1 the photo-electron's total energy in mc^2."""
+    alpha = 1 / 137.035999084
+    g = k + 1.0
+    s = math.sqrt(k * (k + 2.0))  # sqrt(g^2 - 1), without cancellation
+    bracket = 4.0 / 3.0 + g * (g - 2.0) / (g + 1.0) * (1.0 - math.asinh(s) / (g * s))
+    return 1.5 * SIGMA_T * Z ** 5 * alpha ** 4 * k ** -5 * s ** 3 * bracket
+
+
+def test_photoelectric_magnitude_is_the_low_energy_limit_of_sauter():
+    """The oracle's K-shell photoelectric cross-section (the non-relativistic
+    Born form) is the k -> 0 limit of Sauter's relativistic formula, an
+    independent published expression.  Their ratio is 1 + k/4 + O(k^2), so a
+    wrong constant (a dropped sqrt 2, alpha^3, r_e^2 for sigma_T) or a wrong
+    power of Z fails it.  The transcription of Sauter's formula is checked by
+    its own high-energy limit, (3/2) sigma_T Z^5 alpha^4 / k."""
+    alpha = 1 / 137.035999084
+    for symbol in ("O", "Ca"):
+        el = W.Material("pure", ((symbol, 1.0),), 95.0, 1.0)
+        Z, A = el.Z[0], el.A[0]
+        for k in (1e-5, 1e-4, 1e-3):
+            per_atom = oracle.xs("mu_photo", el, k * MC2) * A / 6.02214076e23
+            ratio = per_atom / _sauter_k_shell(Z, k)
+            assert ratio == pytest.approx(1.0 / (1.0 + k / 4.0), rel=5.0 * k * k + 1e-12), (Z, k, ratio)
+        k = 1e7
+        assert _sauter_k_shell(Z, k) * k / (1.5 * SIGMA_T * Z ** 5 * alpha ** 4) == pytest.approx(1.0, rel=1e-5)
+
+
 def test_pair_threshold_and_asymptote():
     for E in (0.5, 1.0, 2 * MC2):
         assert oracle.xs("mu_pair", W.WATER, E) == 0.0
