@@ -155,6 +155,25 @@ def test_ms_screening_moliere_form():
     assert L.om_ms_screening(Z, T) == pytest.approx(eta, rel=1e-14)
 
 
+def test_ms_screening_is_molieres_thomas_fermi_angle():
+    """The screening parameter from its physical definition, by another route
+    than the oracle's closed form: eta = chi_a^2 / 4, with Moliere's screening
+    angle chi_a^2 = chi_0^2 (1.13 + 3.76 (alpha Z / beta)^2), chi_0 = hbar / (p a)
+    the de Broglie wavelength over the Thomas-Fermi radius
+    a = 0.885 a_0 Z^(-1/3) (a_0 the Bohr radius, CODATA 2018; hbar c likewise).
+    A slip between alpha and alpha^2, 0.885 and 0.885^2, or the factor 4 fails."""
+    L = oracle.lib()
+    a0_cm = 0.529177210903e-8
+    hbar_c = 197.3269804e-13  # MeV cm
+    for Z in (1, 8, 20):
+        for T in (0.05, 0.5, 2.0, 15.0):
+            pc = math.sqrt(T * (T + 2 * MC2))
+            beta2 = 1 - 1 / (T / MC2 + 1) ** 2
+            chi0 = hbar_c / (pc * 0.885 * a0_cm * Z ** (-1.0 / 3.0))
+            chia2 = chi0 ** 2 * (1.13 + 3.76 * (Z / 137.035999084) ** 2 / beta2)
+            assert L.om_ms_screening(Z, T) == pytest.approx(chia2 / 4.0, rel=1e-8), (Z, T)
+
+
 def test_ms_mean_mu_series_matches_direct_form():
     L = oracle.lib()
     for a in (990.0, 1000.0, 1010.0):
