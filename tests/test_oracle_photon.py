@@ -54,6 +54,14 @@ def test_klein_nishina_sampler_chi2(k):
     assert chi2_pvalue(cos, kn_density(k), grid) > 0.01
 
 
+def test_water_compton_attenuation_textbook():
+    """Water's Compton mass attenuation coefficient at 1 MeV, where binding
+    effects are negligible and Compton scattering is the whole of the
+    attenuation: the tabulated 0.0707 cm^2/g.  It ties the electron density
+    (electrons per gram) to the Klein-Nishina cross-section."""
+    assert oracle.xs("mu_compton", W.WATER, 1.0) == pytest.approx(0.0707, rel=5e-3)
+
+
 def test_photoelectric_scaling():
     """Born K-shell form: sigma ~ Z^5 k^-7/2 per atom."""
     m = W.WATER
