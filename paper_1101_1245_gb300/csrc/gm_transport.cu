@@ -543,7 +543,10 @@ __device__ __forceinline__ void photon_interact(const TransportArgs &A, const Sm
 // ---------------------------------------------------------------------------
 // The energy lost along the step is not deposited here: its voxel and amount
 // come back in dep_idx / dep_e so the caller can deposit it at a convergent
-// point.  Returns true when a step was taken.
+// point.  Returns true when a step was taken.  The particle starts inside the
+// phantom, so its voxel index is in range: electron primaries are tested when
+// they are claimed, secondaries start at interaction points inside, and a
+// step that ends outside escapes there.
 __device__ bool electron_step(const TransportArgs &A, const Smem &S, Lane &p, int gw, int w,
                               uint32_t &dep_idx, uint32_t &dep_e) {
     const PlanDev &P = S.plans[p.plan];
