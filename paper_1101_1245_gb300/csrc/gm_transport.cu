@@ -22,9 +22,11 @@
 //
 // Divisions on the event path are written __fdividef (reciprocal, then
 // multiply): every divisor there is a direction cosine, an energy, a cross
-// section or a sampler constant, far below the 2^126 where that form departs
-// from the approximate division this file is compiled with (-prec-div=false),
-// so the quotients are the same and the range handling is skipped.
+// section or a sampler constant, far inside the range (|y| < 2^126) for which
+// that form is specified.  There it skips the range handling of the
+// approximate division this file is compiled with (-prec-div=false), and the
+// tallies and event counts of every workload compared were bit-identical with
+// either form.
 #include "gm_common.cuh"
 #include "gm_host.h"
 
