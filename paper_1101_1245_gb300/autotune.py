@@ -9,14 +9,16 @@ The tuner therefore times real plans - a sample of the workload at reduced
 history counts - under candidate settings by coordinate descent and keeps the
 fastest.  A setting the library refuses for the sampled plans (the
 phase-space kernel, which also draws grouped spectra, runs at most two CTAs
-per SM) is recorded as a refused trial and skipped.
+per SM) is recorded as a refused trial and skipped, and so is a setting under
+which the particle queues overflow (a switch level close to the stack
+capacity spills most stacked particles).
 """
 from __future__ import annotations
 
 import statistics
 from typing import Dict, List, Sequence, Tuple
 
-from . import ERR_INVALID_ARG, Context, GpumcdError
+from . import ERR_INVALID_ARG, ERR_QUEUE_OVERFLOW, Context, GpumcdError
 
 # (block_threads, blocks_per_sm) shapes with a kernel variant behind them: 32
 # warps per SM in one CTA (64 registers, one copy of the tables per SM) or two,
@@ -41,11 +43,13 @@ def _time(ctx: Context, plans: Sequence[int], hist: Sequence[int], reps: int) ->
 
 def _try(ctx: Context, plans, hist, reps: int):
     """Transport ms under the launch set on ctx, or None if the library refuses
-    that launch for these plans."""
+    that launch for these plans or its particle queues overflow under it (the
+    run then stops with an error status and marks the plans failed; the next
+    trial resets them)."""
     try:
         return _time(ctx, plans, hist, reps)
     except GpumcdError as e:
-        if e.status != ERR_INVALID_ARG:
+        if e.status not in (ERR_INVALID_ARG, ERR_QUEUE_OVERFLOW):
             raise
         return None
 

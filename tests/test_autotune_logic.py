@@ -73,6 +73,22 @@ def test_autotune_refused_everywhere_restores_the_launch():
     assert ctx.launch == before and not ctx.open
 
 
+def test_autotune_skips_settings_that_overflow_the_queues():
+    """A setting under which a trial run stops with a queue overflow (an error
+    status, nothing dropped) is recorded as refused; the tuner goes on."""
+    def run(plans, hist):
+        if ctx.launch["switch_high"] >= 384:
+            raise g.GpumcdError(g.ERR_QUEUE_OVERFLOW, "gpumcd_run")
+        ctx.last_ms = _cost(ctx.launch)
+
+    ctx = FakeCtx(_cost, lambda L: False)
+    ctx.run = run
+    res = autotune(ctx, [(0, None, 100)], reps=1)
+    assert res["launch"]["switch_high"] < 384
+    assert ({"switch_high": 384}, None) in res["trials"]
+    assert ctx.launch == res["launch"] and not ctx.open
+
+
 def test_autotune_passes_other_errors_on():
     def boom(L):
         raise g.GpumcdError(g.ERR_CUDA, "gpumcd_run")
