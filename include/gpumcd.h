@@ -215,10 +215,14 @@ gpumcd_status gpumcd_create_phantom_device(gpumcd_ctx *ctx, const int32_t dims[3
                                            const float *densities, void *stream,
                                            int32_t *phantom_id);
 
+/* Frees a resident phantom's device memory.  GPUMCD_ERR_NOT_FOUND for an
+ * unknown id, GPUMCD_ERR_STATE while a plan on it is still open. */
 gpumcd_status gpumcd_destroy_phantom(gpumcd_ctx *ctx, int32_t phantom_id);
 
-/* One dose calculation on a resident phantom: n_histories primaries of the
- * source with random streams keyed by seed.  With target_rel_unc > 0 the run
+/* One dose calculation on a resident phantom (GPUMCD §II.C.2: the primaries
+ * of initParticle, then the photon and electron transport of every history;
+ * §II.D: the dose per voxel and its uncertainty by the Delta D estimator):
+ * n_histories primaries of the source with random streams keyed by seed.  With target_rel_unc > 0 the run
  * continues in rounds of n_histories until s_thr (threshold 0.5 D_max) falls
  * to target_rel_unc or max(16 n_histories, 1e9) histories are done.
  * dose_out and sigma_out are host arrays of nx*ny*nz doubles (either may be
