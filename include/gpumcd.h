@@ -248,6 +248,8 @@ gpumcd_status gpumcd_simulate_device(gpumcd_ctx *ctx, int32_t phantom_id,
 gpumcd_status gpumcd_plan_open(gpumcd_ctx *ctx, int32_t phantom_id, const gpumcd_source *source,
                                uint64_t seed, uint32_t n_batches, int32_t *plan_id);
 
+/* Frees a plan's tally and source data.  GPUMCD_ERR_NOT_FOUND for an unknown
+ * id, GPUMCD_ERR_STATE while a submitted sequence holding it is in flight. */
 gpumcd_status gpumcd_plan_close(gpumcd_ctx *ctx, int32_t plan_id);
 
 /* Restarts a plan in place: zeroes its tally and ledger (on `stream`),
@@ -391,6 +393,7 @@ gpumcd_status gpumcd_plan_result_noalloc(gpumcd_ctx *ctx, int32_t plan_id, doubl
  * submitted sequence is in flight (GPUMCD_ERR_STATE).  The launch changes the
  * speed of a run, never its result. */
 gpumcd_status gpumcd_set_launch(gpumcd_ctx *ctx, const gpumcd_launch *launch);
+/* Copies the context's current launch into *launch (host memory). */
 gpumcd_status gpumcd_get_launch(gpumcd_ctx *ctx, gpumcd_launch *launch);
 
 /* ---- diagnostics used by the tests ------------------------------------- */
