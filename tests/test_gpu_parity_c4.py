@@ -178,34 +178,35 @@ def test_batched_workload_plans_against_oracle():
             assert g_rate == pytest.approx(o_rate, rel=0.03), (t, k, g_rate, o_rate)
 
 
-def test_batched_workload_electron_plan_gamma():
-    """Gamma 2% / 2 mm (voxels above 20% of D_max, the oracle as reference)
-    on plan 28 of the batched workload: 84^3 voxels of 0.467 cm with
-    smoothed-noise densities of 0.2 to 2.0 g/cm^3, a 12.5 MeV electron field of
-    10.7 cm.  The oracle runs 8e6 histories, which brings its noise in the
-    high-dose region under 1% of D_max; the GPU five times more.  (A photon
-    plan would need over 1e8 oracle histories for that: its low-density voxels
-    see few interactions.)"""
+@pytest.mark.parametrize("index,n,n_ora", [(28, 84, 8_000_000), (14, 64, 3_000_000)])
+def test_batched_workload_electron_plan_gamma(index, n, n_ora):
+    """Gamma 2% / 2 mm (voxels above 20% of D_max, the oracle as reference) on
+    electron plans of the batched workload: plan 28, 84^3 voxels of 0.467 cm
+    with a 12.5 MeV field of 10.7 cm, and plan 14, 64^3 voxels of 0.377 cm with
+    a 7.1 MeV field of 3.9 cm, both on smoothed-noise densities of 0.2 to 2.0
+    g/cm^3.  The oracle's histories bring its noise in the high-dose region
+    under 1% of D_max; the GPU runs five times more.  (A photon plan would need
+    over 1e8 oracle histories for that: its low-density voxels see few
+    interactions.)"""
     import torch
 
-    sp = W.config4()[28]
-    assert sp.particle == W.ELECTRON and sp.n == 84
+    sp = W.config4()[index]
+    assert sp.particle == W.ELECTRON and sp.n == n
     ph = sp.phantom()
     src = W.square_field(sp.particle, sp.energy, ph, sp.field_cm)
     ctx = make_ctx()
     pid = ctx.create_phantom(ph)
     plan = ctx.plan_open(pid, src, sp.seed, 16)
-    ctx.run([plan], [40_000_000])
+    ctx.run([plan], [5 * n_ora])
     d = torch.zeros(ph.nvox, dtype=torch.float64, device="cuda")
     s = torch.zeros_like(d)
     st = ctx.plan_result(plan, 0.5, d.data_ptr(), s.data_ptr())
     assert ledger_exact(st)
     dg, sg = d.cpu().numpy(), s.cpu().numpy()
     ctx.close()
-    ora = oracle.simulate(W.MATERIALS, W.DEFAULT_PHYSICS, ph, src, 8_000_000, 123, processes=host_cores())
+    ora = oracle.simulate(W.MATERIALS, W.DEFAULT_PHYSICS, ph, src, n_ora, 123, processes=host_cores())
     do, so = ora.dose_gy(ph), ora.sigma_gy(ph)
     noise = float(np.median(so[do > 0.5 * do.max()] / do.max()))
-    n = sp.n
     rate = gamma_pass_rate(do.reshape(n, n, n), dg.reshape(n, n, n), (10.0 * sp.voxel_cm,) * 3)
     assert noise < 0.01, (noise, rate)
     assert three_sigma_pass_rate(dg, sg, do, so, dg > 0.1 * dg.max()) >= 0.99
